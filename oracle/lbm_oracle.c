@@ -1,0 +1,647 @@
+/*
+ * lbm_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * Plain, slow, obviously-correct FP64 oracle of the D2Q9 two-phase
+ * colour-gradient lattice Boltzmann step of arXiv 1903.01168, Sec. 2.  It
+ * follows the paper's operators one by one, in the paper's order and
+ * notation, with no fusion and no reordering:
+ *
+ *   moments and colour field  Sec. 2.1, Eq. (eq:color_field)
+ *   colour gradient F         Eq. (eq:colorGradient)
+ *   omega_eff, A              Sec. 2.1 (interpolation), Eq. (eq:sigmaIsoAllen)
+ *   collision per colour      Eq. (eq:singleCollision) / Eq. (eq:singleCollisionMRT),
+ *                             equilibrium Eq. (eq:equilibrium) / Eq. (eq:equilibrium_hermite),
+ *                             source U^k = M^-1 C^k (Sec. 2.1, NS recovery),
+ *                             Guo body force (not given by the paper; reading below)
+ *   perturbation per colour   Eq. (eq:perturbation)
+ *   recolouring               Eq. (eq:recoloringOperator)
+ *   streaming + boundaries    Eq. (eq:subop4), Sec. 2.5 (bounce-back, periodic,
+ *                             two-phase Zou-He inlet / outlet)
+ *
+ * Readings taken where the paper is silent, garbled or self-contradictory
+ * (each is listed in the design notes of the repository):
+ *   - direction order is the standard one of the appendix matrices; every
+ *     per-direction constant (W, phi, xi, B) is keyed by |c_i|^2, not by the
+ *     index parity of the printed velocity formula;
+ *   - gamma = (1 - alpha_b) / (1 - alpha_r), i.e. alpha_r = 1 - (1 - alpha_b)/gamma,
+ *     so that both pure phases at rest have the same pressure;
+ *   - psi = +1 in pure red, as Eq. (eq:color_field) gives;
+ *   - the Hermite factor "(3 c_i - 4)" is (3 |c_i|^2 - 4);
+ *   - A = 9 sigma omega_eff / 4 per node, from Eq. (eq:sigmaIsoAllen);
+ *   - the perturbation term is added to each colour (two colours, one l != k
+ *     term each), as Eq. (eq:perturbation) is printed;
+ *   - the recolouring term is zero when i = 0 or |F| == 0 exactly;
+ *   - Guo-Zheng-Shi forcing with F^k = rho_k g and u = (sum N c + rho g / 2) / rho;
+ *   - halfway bounce-back; psi on a node outside the domain is the
+ *     W-weighted mean of its in-domain neighbours (the wetting extrapolation of
+ *     Sec. 2.4 without the stray c_{i alpha} factor);
+ *   - the paper's north inlet / south outlet are rotated to a west inlet /
+ *     east outlet; the inlet phase is prescribed, the outlet colour fraction
+ *     comes from the known populations, the outlet velocity is
+ *     v = -1 + (...)/rho_out and rho_out mixes the pure-phase densities by
+ *     colour fraction.
+ */
+#include "lbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- lattice */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+static int c2(int i) { return CX[i] * CX[i] + CY[i] * CY[i]; }
+
+/* D2Q9 weights W_i (Sec. 2.1). */
+static double W(int i) {
+    int n = c2(i);
+    return n == 0 ? 4.0 / 9.0 : (n == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+/* Rest weights phi^k_i of the density-ratio equilibrium (Sec. 2.1). */
+static double phi(double alpha, int i) {
+    int n = c2(i);
+    return n == 0 ? alpha : (n == 1 ? (1.0 - alpha) / 5.0 : (1.0 - alpha) / 20.0);
+}
+
+/* S2I4 gradient weights xi_i, Eq. (eq:colorGradient). */
+static double xi(int i) {
+    int n = c2(i);
+    return n == 0 ? 0.0 : (n == 1 ? 1.0 / 3.0 : 1.0 / 12.0);
+}
+
+/* Perturbation constants B_i, Eq. (eq:perturbation). */
+static double Bc(int i) {
+    int n = c2(i);
+    return n == 0 ? -4.0 / 27.0 : (n == 1 ? 2.0 / 27.0 : 5.0 / 108.0);
+}
+
+/* ------------------------------------------------------------- parameters */
+void orc_derived(const orc_params *p, double *alpha_r, double *omega_r, double *omega_b,
+                 double *chi, double *eta, double *kappa, double *lam, double *nu) {
+    double ar = 1.0 - (1.0 - p->alpha_b) / p->gamma;    /* Eq. (eq:gammaAlphaBeta) */
+    double wr = 1.0 / p->tau_r, wb = 1.0 / p->tau_b;
+    double c = 2.0 * wr * wb / (wr + wb);
+    double e = 2.0 * (wr - c) / p->delta;
+    double l = 2.0 * (c - wb) / p->delta;
+    if (alpha_r) *alpha_r = ar;
+    if (omega_r) *omega_r = wr;
+    if (omega_b) *omega_b = wb;
+    if (chi) *chi = c;
+    if (eta) *eta = e;
+    if (kappa) *kappa = -e / (2.0 * p->delta);
+    if (lam) *lam = l;
+    if (nu) *nu = l / (2.0 * p->delta);
+}
+
+static double alpha_of(const orc_params *p, int k) {
+    double ar;
+    orc_derived(p, &ar, 0, 0, 0, 0, 0, 0, 0);
+    return k == 0 ? ar : p->alpha_b;
+}
+
+static double rho0_of(const orc_params *p, int k) { return k == 0 ? p->gamma : 1.0; }
+
+/* (c_s^k)^2 = 3 (1 - alpha_k) / 5, Eq. (eq:pressureRelation). */
+static double cs2_of(const orc_params *p, int k) { return 3.0 * (1.0 - alpha_of(p, k)) / 5.0; }
+
+/* --------------------------------------------------------------- operators */
+
+/* Eq. (eq:equilibrium), or Eq. (eq:equilibrium_hermite) with the factor read
+ * as (3|c_i|^2 - 4). */
+void orc_equilibrium(const orc_params *p, int k, double rho_k, double ux, double uy,
+                     double *neq) {
+    double alpha = alpha_of(p, k);
+    double cs2 = cs2_of(p, k);
+    double usq = ux * ux + uy * uy;
+    for (int i = 0; i < 9; i++) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        double lin = 3.0 * cu;
+        if (p->equilibrium == ORC_EQ_HERMITE)
+            lin = 3.0 * cu * (1.0 + 0.5 * (3.0 * cs2 - 1.0) * (3.0 * c2(i) - 4.0));
+        neq[i] = rho_k * phi(alpha, i) + rho_k * W(i) * (lin + 4.5 * cu * cu - 1.5 * usq);
+    }
+}
+
+/* Piecewise omega_eff(psi) of Sec. 2.1, with f_r and f_b as printed. */
+double orc_omega_eff(const orc_params *p, double psi) {
+    double wr, wb, chi, eta, kappa, lam, nu;
+    orc_derived(p, 0, &wr, &wb, &chi, &eta, &kappa, &lam, &nu);
+    if (psi > p->delta) return wr;
+    if (psi > 0.0) return chi + eta * psi + kappa * psi * psi;
+    if (psi >= -p->delta) return chi + lam * psi + nu * psi * psi;
+    return wb;
+}
+
+/* One colour's increment (A/2)|F| [W_i (F.c_i)^2/|F|^2 - B_i], Eq. (eq:perturbation).
+ * Zero when |F| == 0. */
+void orc_perturbation(const orc_params *p, double A, double Fx, double Fy, double *dN) {
+    (void)p;
+    double F2 = Fx * Fx + Fy * Fy;
+    for (int i = 0; i < 9; i++) {
+        if (F2 == 0.0) {
+            dN[i] = 0.0;
+            continue;
+        }
+        double Fn = sqrt(F2);
+        double Fc = Fx * CX[i] + Fy * CY[i];
+        dN[i] = 0.5 * A * Fn * (W(i) * Fc * Fc / F2 - Bc(i));
+    }
+}
+
+/* Eq. (eq:recoloringOperator): N^r_i = rho_r/rho N_i + beta rho_r rho_b/rho^2 cos(phi_i)
+ * sum_k N^{k(e)}_i(rho_k, 0, alpha_k); N^b_i = N_i - N^r_i.  The second term is
+ * zero for i = 0 or |F| == 0. */
+void orc_recolour(const orc_params *p, double rho_r, double rho_b, double Fx, double Fy,
+                  const double *N, double *Nr, double *Nb) {
+    double rho = rho_r + rho_b;
+    double F2 = Fx * Fx + Fy * Fy;
+    double ar = alpha_of(p, 0), ab = alpha_of(p, 1);
+    for (int i = 0; i < 9; i++) {
+        double term = 0.0;
+        if (i != 0 && F2 != 0.0) {
+            double cosphi = (CX[i] * Fx + CY[i] * Fy) / (sqrt((double)c2(i)) * sqrt(F2));
+            double rest = rho_r * phi(ar, i) + rho_b * phi(ab, i); /* N^{k(e)}(rho_k, 0) summed */
+            term = p->beta * rho_r * rho_b / (rho * rho) * cosphi * rest;
+        }
+        Nr[i] = rho_r / rho * N[i] + term;
+        Nb[i] = rho_b / rho * N[i] - term;
+    }
+}
+
+/* The appendix "Transformation matrices": M and M^{-1} = (1/36) * (integer matrix). */
+static const int M_INT[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+static const int MINV36[9][9] = {
+    {4, -4, 4, 0, 0, 0, 0, 0, 0},
+    {4, -1, -2, 6, -6, 0, 0, 9, 0},
+    {4, -1, -2, 0, 0, 6, -6, -9, 0},
+    {4, -1, -2, -6, 6, 0, 0, 9, 0},
+    {4, -1, -2, 0, 0, -6, 6, -9, 0},
+    {4, 2, 1, 6, 3, 6, 3, 0, 9},
+    {4, 2, 1, -6, -3, 6, 3, 0, -9},
+    {4, 2, 1, -6, -3, -6, -3, 0, 9},
+    {4, 2, 1, 6, 3, -6, -3, 0, -9}};
+
+void orc_mrt_matrices(double *M, double *Minv) {
+    for (int a = 0; a < 9; a++)
+        for (int b = 0; b < 9; b++) {
+            M[a * 9 + b] = (double)M_INT[a][b];
+            Minv[a * 9 + b] = (double)MINV36[a][b] / 36.0;
+        }
+}
+
+static void matvec(const double *A, const double *x, double *y) {
+    for (int a = 0; a < 9; a++) {
+        double s = 0.0;
+        for (int b = 0; b < 9; b++) s += A[a * 9 + b] * x[b];
+        y[a] = s;
+    }
+}
+
+/* Node moments: rho_k, rho, and u = (sum_k sum_i N^k_i c_i + rho g / 2) / rho. */
+static void node_moments(const orc_params *p, const double *Nk, double *rho_r, double *rho_b,
+                         double *ux, double *uy) {
+    double rr = 0.0, rb = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; i++) {
+        rr += Nk[i];
+        rb += Nk[9 + i];
+        jx += (Nk[i] + Nk[9 + i]) * CX[i];
+        jy += (Nk[i] + Nk[9 + i]) * CY[i];
+    }
+    double rho = rr + rb;
+    *rho_r = rr;
+    *rho_b = rb;
+    *ux = (jx + 0.5 * rho * p->gx) / rho;
+    *uy = (jy + 0.5 * rho * p->gy) / rho;
+}
+
+static double colour_field(const orc_params *p, double rho_r, double rho_b) {
+    double a = rho_r / rho0_of(p, 0), b = rho_b / rho0_of(p, 1);
+    return (a - b) / (a + b);                           /* Eq. (eq:color_field) */
+}
+
+/* Single-phase collision of each colour (BGK or MRT, + Guo, + U^k) followed by
+ * the perturbation of each colour.  Input: pre-collision N^k_i of one node,
+ * the colour gradient F and, for the Hermite/MRT source, the divergence parts
+ * d_x Q^k_x and d_y Q^k_y of each colour. */
+void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double Fy,
+                      double divQr_x, double divQr_y, double divQb_x, double divQb_y,
+                      double *Nstar) {
+    double rho_r, rho_b, ux, uy;
+    node_moments(p, Nk, &rho_r, &rho_b, &ux, &uy);
+    double psi = colour_field(p, rho_r, rho_b);
+    double w = orc_omega_eff(p, psi);
+    double A = 9.0 * p->sigma * w / 4.0;                /* Eq. (eq:sigmaIsoAllen) */
+    double M[81], Minv[81];
+    orc_mrt_matrices(M, Minv);
+    double s[9];
+    for (int a = 0; a < 9; a++) s[a] = p->mrt_lambda * w; /* s_0..s_6 */
+    s[7] = w;
+    s[8] = w;
+
+    for (int k = 0; k < 2; k++) {
+        const double *N = Nk + 9 * k;
+        double *out = Nstar + 9 * k;
+        double rho_k = k == 0 ? rho_r : rho_b;
+        double neq[9];
+        orc_equilibrium(p, k, rho_k, ux, uy, neq);
+
+        /* Guo source of colour k, force F^k = rho_k g. */
+        double fx = rho_k * p->gx, fy = rho_k * p->gy;
+        double src[9];
+        for (int i = 0; i < 9; i++) {
+            double cu = CX[i] * ux + CY[i] * uy;
+            src[i] = W(i) * (3.0 * ((CX[i] - ux) * fx + (CY[i] - uy) * fy) +
+                             9.0 * cu * (CX[i] * fx + CY[i] * fy));
+        }
+
+        if (p->collision == ORC_BGK) {
+            /* Eq. (eq:singleCollision) + (1 - omega/2) S_i */
+            for (int i = 0; i < 9; i++)
+                out[i] = N[i] - w * (N[i] - neq[i]) + (1.0 - 0.5 * w) * src[i];
+        } else {
+            /* Eq. (eq:singleCollisionMRT): N - M^-1 S M (N - Neq) + M^-1 (I - S/2) M src + U^k */
+            double d[9], m[9], ms[9], t[9], back[9];
+            for (int i = 0; i < 9; i++) d[i] = N[i] - neq[i];
+            matvec(M, d, m);
+            matvec(M, src, ms);
+            for (int a = 0; a < 9; a++) t[a] = s[a] * m[a] - (1.0 - 0.5 * s[a]) * ms[a];
+            if (p->equilibrium == ORC_EQ_HERMITE) {
+                /* C^k = [0, C_1, 0, 0, 0, 0, 0, C_7, 0]; U^k = M^-1 C^k is ADDED, so it
+                 * enters t with a minus sign. */
+                double dqx = k == 0 ? divQr_x : divQb_x;
+                double dqy = k == 0 ? divQr_y : divQb_y;
+                double C1 = 3.0 * (1.0 - 0.5 * s[1]) * (dqx + dqy);
+                double C7 = 3.0 * (1.0 - 0.5 * w) * (dqx + p->c7_sign * dqy);
+                t[1] -= C1;
+                t[7] -= C7;
+            }
+            matvec(Minv, t, back);
+            for (int i = 0; i < 9; i++) out[i] = N[i] - back[i];
+        }
+
+        /* Eq. (eq:perturbation): one l != k term per colour. */
+        if (p->perturb_mode == ORC_PERTURB_PER_COLOUR) {
+            double dN[9];
+            orc_perturbation(p, A, Fx, Fy, dN);
+            for (int i = 0; i < 9; i++) out[i] += dN[i];
+        }
+    }
+    if (p->perturb_mode == ORC_PERTURB_ONCE) {
+        /* Alternative reading: one A/2 term on the colour-blind distribution
+         * (put on the red set; only the colour-blind sum is used afterwards). */
+        double dN[9];
+        orc_perturbation(p, A, Fx, Fy, dN);
+        for (int i = 0; i < 9; i++) Nstar[i] += dN[i];
+    }
+}
+
+/* ----------------------------------------------------------- Zou-He (Sec. 2.5) */
+
+/* West velocity inlet, the paper's north inlet rotated by +90 degrees.  On
+ * entry Nr/Nb hold the post-streaming populations with the unknowns 1, 5, 8
+ * undefined; f_r is the red fraction of the injected phase at this node. */
+void orc_zouhe_inlet(const orc_params *p, double f_r, double *Nr, double *Nb) {
+    double f_b = 1.0 - f_r;
+    double N[9];
+    for (int i = 0; i < 9; i++) N[i] = Nr[i] + Nb[i];
+    double Vx = f_r * p->u_in_r + f_b * p->u_in_b; /* v^in = v^{b,in} + v^{r,in} */
+    double Vy = 0.0;
+    double rho = (N[0] + N[2] + N[4] + 2.0 * (N[3] + N[6] + N[7])) / (1.0 - Vx);
+    double H = 0.0;
+    if (p->equilibrium == ORC_EQ_HERMITE) {
+        double amix = f_r * (3.0 * cs2_of(p, 0) - 1.0) + f_b * (3.0 * cs2_of(p, 1) - 1.0);
+        H = -rho * amix * Vx / 3.0;
+    }
+    N[1] = N[3] + 2.0 / 3.0 * rho * Vx + H;
+    N[5] = N[7] + 0.5 * (N[4] - N[2]) + 0.5 * rho * Vy + rho * Vx / 6.0 - 0.5 * H;
+    N[8] = N[6] + 0.5 * (N[2] - N[4]) - 0.5 * rho * Vy + rho * Vx / 6.0 - 0.5 * H;
+    const int unk[3] = {1, 5, 8};
+    for (int j = 0; j < 3; j++) {
+        Nr[unk[j]] = f_r * N[unk[j]];
+        Nb[unk[j]] = f_b * N[unk[j]];
+    }
+}
+
+/* East pressure outlet, the paper's south outlet rotated by +90 degrees.
+ * Unknowns 3, 6, 7.  The colour fraction comes from the known populations. */
+void orc_zouhe_outlet(const orc_params *p, double *Nr, double *Nb) {
+    const int known[6] = {0, 1, 2, 4, 5, 8};
+    double kr = 0.0, kb = 0.0;
+    for (int j = 0; j < 6; j++) {
+        kr += Nr[known[j]];
+        kb += Nb[known[j]];
+    }
+    double psi = colour_field(p, kr, kb);
+    double f_r = 0.5 * (1.0 + psi), f_b = 1.0 - f_r;
+    double N[9];
+    for (int i = 0; i < 9; i++) N[i] = Nr[i] + Nb[i];
+    double rho = f_b * p->p_out / cs2_of(p, 1) + f_r * p->p_out / cs2_of(p, 0);
+    double Vx = -1.0 + (N[0] + N[2] + N[4] + 2.0 * (N[1] + N[5] + N[8])) / rho;
+    double H = 0.0;
+    if (p->equilibrium == ORC_EQ_HERMITE) {
+        double amix = f_r * (3.0 * cs2_of(p, 0) - 1.0) + f_b * (3.0 * cs2_of(p, 1) - 1.0);
+        H = rho * amix * Vx / 3.0;
+    }
+    /* tangential outlet velocity is zero (v^out_x = 0 in the paper's frame) */
+    N[3] = N[1] - 2.0 / 3.0 * rho * Vx + H;
+    N[6] = N[8] - 0.5 * (N[2] - N[4]) - rho * Vx / 6.0 - 0.5 * H;
+    N[7] = N[5] + 0.5 * (N[2] - N[4]) - rho * Vx / 6.0 - 0.5 * H;
+    const int unk[3] = {3, 6, 7};
+    for (int j = 0; j < 3; j++) {
+        Nr[unk[j]] = f_r * N[unk[j]];
+        Nb[unk[j]] = f_b * N[unk[j]];
+    }
+}
+
+/* ------------------------------------------------------------------ state */
+struct orc_sim {
+    orc_params p;
+    long t;
+    double *N;     /* pre-collision N^k_i(x, t) */
+    double *Npost; /* after collision, perturbation and recolouring */
+    double *rho_r, *rho_b, *ux, *uy, *psi;
+    double *Qx, *Qy; /* Q^k per colour: [k][y][x] */
+};
+
+static size_t pidx(const orc_sim *s, int k, int i, int x, int y) {
+    return (((size_t)(k * 9 + i) * s->p.ny + y) * s->p.nx) + x;
+}
+
+orc_sim *orc_create(const orc_params *p) {
+    orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
+    s->p = *p;
+    size_t n = (size_t)p->nx * p->ny;
+    s->N = (double *)calloc(18 * n, sizeof(double));
+    s->Npost = (double *)calloc(18 * n, sizeof(double));
+    s->rho_r = (double *)calloc(n, sizeof(double));
+    s->rho_b = (double *)calloc(n, sizeof(double));
+    s->ux = (double *)calloc(n, sizeof(double));
+    s->uy = (double *)calloc(n, sizeof(double));
+    s->psi = (double *)calloc(n, sizeof(double));
+    s->Qx = (double *)calloc(2 * n, sizeof(double));
+    s->Qy = (double *)calloc(2 * n, sizeof(double));
+    return s;
+}
+
+void orc_destroy(orc_sim *s) {
+    if (!s) return;
+    free(s->N);
+    free(s->Npost);
+    free(s->rho_r);
+    free(s->rho_b);
+    free(s->ux);
+    free(s->uy);
+    free(s->psi);
+    free(s->Qx);
+    free(s->Qy);
+    free(s);
+}
+
+long orc_time(const orc_sim *s) { return s->t; }
+
+void orc_set_pops(orc_sim *s, const double *pop) {
+    memcpy(s->N, pop, 18 * (size_t)s->p.nx * s->p.ny * sizeof(double));
+}
+
+void orc_get_pops(const orc_sim *s, double *pop) {
+    memcpy(pop, s->N, 18 * (size_t)s->p.nx * s->p.ny * sizeof(double));
+}
+
+static void gather_node(const orc_sim *s, const double *pop, int x, int y, double *Nk) {
+    for (int k = 0; k < 2; k++)
+        for (int i = 0; i < 9; i++) Nk[9 * k + i] = pop[pidx(s, k, i, x, y)];
+}
+
+static void scatter_node(orc_sim *s, double *pop, int x, int y, const double *Nk) {
+    for (int k = 0; k < 2; k++)
+        for (int i = 0; i < 9; i++) pop[pidx(s, k, i, x, y)] = Nk[9 * k + i];
+}
+
+/* Red fraction injected at inlet row y at time t. */
+static double inlet_red_fraction(const orc_params *p, int y, long t) {
+    if (p->inlet_mode == ORC_INLET_LAYERED) return y < p->inlet_layer ? 1.0 : 0.0;
+    long period = (long)p->inlet_period_r + p->inlet_period_b;
+    if (period <= 0) return 1.0;
+    return (t % period) < p->inlet_period_r ? 1.0 : 0.0;
+}
+
+static void apply_inout(orc_sim *s) {
+    if (s->p.bc_x != ORC_INOUT) return;
+    for (int y = 0; y < s->p.ny; y++) {
+        double Nk[18];
+        gather_node(s, s->N, 0, y, Nk);
+        orc_zouhe_inlet(&s->p, inlet_red_fraction(&s->p, y, s->t), Nk, Nk + 9);
+        scatter_node(s, s->N, 0, y, Nk);
+        gather_node(s, s->N, s->p.nx - 1, y, Nk);
+        orc_zouhe_outlet(&s->p, Nk, Nk + 9);
+        scatter_node(s, s->N, s->p.nx - 1, y, Nk);
+    }
+}
+
+void orc_init_fields(orc_sim *s, const double *rho_r, const double *rho_b, const double *ux,
+                     const double *uy) {
+    int nx = s->p.nx, ny = s->p.ny;
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t n = (size_t)y * nx + x;
+            double er[9], eb[9];
+            orc_equilibrium(&s->p, 0, rho_r[n], ux[n], uy[n], er);
+            orc_equilibrium(&s->p, 1, rho_b[n], ux[n], uy[n], eb);
+            for (int i = 0; i < 9; i++) {
+                s->N[pidx(s, 0, i, x, y)] = er[i];
+                s->N[pidx(s, 1, i, x, y)] = eb[i];
+            }
+        }
+    s->t = 0;
+    apply_inout(s);
+}
+
+/* Is (X, Y) inside the domain after periodic wrapping?  Writes the wrapped
+ * coordinates. */
+static int in_domain(const orc_params *p, int X, int Y, int *xw, int *yw) {
+    if (X < 0 || X >= p->nx) {
+        if (p->bc_x != ORC_PERIODIC) return 0;
+        X = ((X % p->nx) + p->nx) % p->nx;
+    }
+    if (Y < 0 || Y >= p->ny) {
+        if (p->bc_y != ORC_PERIODIC) return 0;
+        Y = ((Y % p->ny) + p->ny) % p->ny;
+    }
+    *xw = X;
+    *yw = Y;
+    return 1;
+}
+
+/* psi at any lattice position next to the domain (Sec. 2.4 extrapolation for
+ * nodes outside the domain). */
+static double psi_at(const orc_sim *s, int X, int Y) {
+    int xw, yw;
+    if (in_domain(&s->p, X, Y, &xw, &yw)) return s->psi[(size_t)yw * s->p.nx + xw];
+    double num = 0.0, den = 0.0;
+    for (int i = 1; i < 9; i++)
+        if (in_domain(&s->p, X + CX[i], Y + CY[i], &xw, &yw)) {
+            num += W(i) * s->psi[(size_t)yw * s->p.nx + xw];
+            den += W(i);
+        }
+    return den > 0.0 ? num / den : 0.0;
+}
+
+/* Q^k (component comp: 0 x, 1 y) at any lattice position next to the domain:
+ * zero behind a no-slip wall, extrapolated like psi behind an inlet/outlet. */
+static double Q_at(const orc_sim *s, int k, int comp, int X, int Y) {
+    const double *Q = comp == 0 ? s->Qx : s->Qy;
+    size_t n = (size_t)s->p.nx * s->p.ny;
+    int xw, yw;
+    if (in_domain(&s->p, X, Y, &xw, &yw)) return Q[k * n + (size_t)yw * s->p.nx + xw];
+    int out_y = (Y < 0 || Y >= s->p.ny);
+    int out_x = (X < 0 || X >= s->p.nx);
+    if ((out_y && s->p.bc_y == ORC_WALL) || (out_x && s->p.bc_x == ORC_WALL)) return 0.0;
+    double num = 0.0, den = 0.0;
+    for (int i = 1; i < 9; i++)
+        if (in_domain(&s->p, X + CX[i], Y + CY[i], &xw, &yw)) {
+            num += W(i) * Q[k * n + (size_t)yw * s->p.nx + xw];
+            den += W(i);
+        }
+    return den > 0.0 ? num / den : 0.0;
+}
+
+/* Moments, colour field and Q^k of every node of the current state. */
+static void moments_pass(orc_sim *s) {
+    const orc_params *p = &s->p;
+    int nx = p->nx, ny = p->ny;
+    size_t n = (size_t)nx * ny;
+    double ar = alpha_of(p, 0), ab = alpha_of(p, 1);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t c = (size_t)y * nx + x;
+            double Nk[18];
+            gather_node(s, s->N, x, y, Nk);
+            node_moments(p, Nk, &s->rho_r[c], &s->rho_b[c], &s->ux[c], &s->uy[c]);
+            s->psi[c] = colour_field(p, s->rho_r[c], s->rho_b[c]);
+            /* Q^k = (1.8 alpha_k - 0.8) rho_k u (Sec. 2.1, NS recovery) */
+            s->Qx[c] = (1.8 * ar - 0.8) * s->rho_r[c] * s->ux[c];
+            s->Qy[c] = (1.8 * ar - 0.8) * s->rho_r[c] * s->uy[c];
+            s->Qx[n + c] = (1.8 * ab - 0.8) * s->rho_b[c] * s->ux[c];
+            s->Qy[n + c] = (1.8 * ab - 0.8) * s->rho_b[c] * s->uy[c];
+        }
+}
+
+/* Colour gradient F (Eq. (eq:colorGradient)) and the S2I4 derivatives
+ * d_x Q^k_x, d_y Q^k_y of one node, from the fields of moments_pass. */
+static void gradient_node(const orc_sim *s, int x, int y, double *Fx, double *Fy,
+                          double dQ[2][2]) {
+    *Fx = 0.0;
+    *Fy = 0.0;
+    dQ[0][0] = dQ[0][1] = dQ[1][0] = dQ[1][1] = 0.0;
+    for (int i = 1; i < 9; i++) {
+        double ps = psi_at(s, x + CX[i], y + CY[i]);
+        *Fx += xi(i) * CX[i] * ps;
+        *Fy += xi(i) * CY[i] * ps;
+        for (int k = 0; k < 2; k++) {
+            dQ[k][0] += xi(i) * CX[i] * Q_at(s, k, 0, x + CX[i], y + CY[i]);
+            dQ[k][1] += xi(i) * CY[i] * Q_at(s, k, 1, x + CX[i], y + CY[i]);
+        }
+    }
+}
+
+void orc_gradient_fields(orc_sim *s, double *Fx, double *Fy, double *dQ) {
+    moments_pass(s);
+    int nx = s->p.nx, ny = s->p.ny;
+    size_t n = (size_t)nx * ny;
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t c = (size_t)y * nx + x;
+            double fx, fy, d[2][2];
+            gradient_node(s, x, y, &fx, &fy, d);
+            if (Fx) Fx[c] = fx;
+            if (Fy) Fy[c] = fy;
+            if (dQ) {
+                dQ[c] = d[0][0];
+                dQ[n + c] = d[0][1];
+                dQ[2 * n + c] = d[1][0];
+                dQ[3 * n + c] = d[1][1];
+            }
+        }
+}
+
+static void step_once(orc_sim *s) {
+    const orc_params *p = &s->p;
+    int nx = p->nx, ny = p->ny;
+
+    /* 1. moments and colour field of every node at time t */
+    moments_pass(s);
+
+    /* 2. colour gradient, collision, perturbation, recolouring per node */
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t c = (size_t)y * nx + x;
+            double Fx, Fy, dQ[2][2];
+            gradient_node(s, x, y, &Fx, &Fy, dQ);
+            double Nk[18], Nstar[18], Nsum[9], Nr[9], Nb[9];
+            gather_node(s, s->N, x, y, Nk);
+            orc_collide_node(p, Nk, Fx, Fy, dQ[0][0], dQ[0][1], dQ[1][0], dQ[1][1], Nstar);
+            for (int i = 0; i < 9; i++) Nsum[i] = Nstar[i] + Nstar[9 + i];
+            orc_recolour(p, s->rho_r[c], s->rho_b[c], Fx, Fy, Nsum, Nr, Nb);
+            for (int i = 0; i < 9; i++) {
+                s->Npost[pidx(s, 0, i, x, y)] = Nr[i];
+                s->Npost[pidx(s, 1, i, x, y)] = Nb[i];
+            }
+        }
+
+    /* 3. streaming, Eq. (eq:subop4), with periodic / bounce-back links */
+    for (int k = 0; k < 2; k++)
+        for (int i = 0; i < 9; i++)
+            for (int y = 0; y < ny; y++)
+                for (int x = 0; x < nx; x++) {
+                    int X = x - CX[i], Y = y - CY[i];
+                    int xw, yw;
+                    double v;
+                    int out_y = (Y < 0 || Y >= ny), out_x = (X < 0 || X >= nx);
+                    if (in_domain(p, X, Y, &xw, &yw))
+                        v = s->Npost[pidx(s, k, i, xw, yw)];
+                    else if ((out_y && p->bc_y == ORC_WALL) || (out_x && p->bc_x == ORC_WALL))
+                        v = s->Npost[pidx(s, k, OPP[i], x, y)]; /* halfway bounce-back */
+                    else
+                        v = 0.0; /* unknown, set by Zou-He below */
+                    s->N[pidx(s, k, i, x, y)] = v;
+                }
+    s->t += 1;
+
+    /* 4. two-phase Zou-He columns of the new state */
+    apply_inout(s);
+}
+
+void orc_step(orc_sim *s, long n) {
+    for (long j = 0; j < n; j++) step_once(s);
+}
+
+void orc_fields(const orc_sim *s, double *rho_r, double *rho_b, double *ux, double *uy,
+                double *p, double *psi) {
+    int nx = s->p.nx, ny = s->p.ny;
+    double cr = cs2_of(&s->p, 0), cb = cs2_of(&s->p, 1);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            size_t c = (size_t)y * nx + x;
+            double Nk[18], rr, rb, vx, vy;
+            gather_node(s, s->N, x, y, Nk);
+            node_moments(&s->p, Nk, &rr, &rb, &vx, &vy);
+            if (rho_r) rho_r[c] = rr;
+            if (rho_b) rho_b[c] = rb;
+            if (ux) ux[c] = vx;
+            if (uy) uy[c] = vy;
+            if (p) p[c] = rr * cr + rb * cb;
+            if (psi) psi[c] = colour_field(&s->p, rr, rb);
+        }
+}
