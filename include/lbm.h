@@ -1,0 +1,204 @@
+/*
+ * lbm.h -- C ABI of the GB300 two-phase colour-gradient lattice Boltzmann library.
+ *
+ * The library advances D2Q9 two-phase colour-gradient LBM simulations
+ * (arXiv 1903.01168, Sec. 2) on one NVIDIA GB300 (sm_103a) with hand-written
+ * CUDA kernels.  One time step applies, per node and per colour k in {red,
+ * blue}:
+ *   1. collision, Eq. (eq:singleCollision) (BGK) or Eq. (eq:singleCollisionMRT)
+ *      (MRT), towards Eq. (eq:equilibrium) or the Hermite equilibrium
+ *      Eq. (eq:equilibrium_hermite) (+ the source U^k = M^-1 C^k under MRT),
+ *      with the interpolated relaxation rate omega_eff(psi) of Sec. 2.1 and a
+ *      Guo body force F^k = rho_k g;
+ *   2. the surface-tension perturbation, Eq. (eq:perturbation), driven by the
+ *      S2I4 colour gradient F of Eq. (eq:colorGradient), A = 9 sigma omega_eff / 4
+ *      (Eq. (eq:sigmaIsoAllen));
+ *   3. recolouring, Eq. (eq:recoloringOperator);
+ *   4. streaming, Eq. (eq:subop4), with periodic ends, halfway bounce-back
+ *      walls and the two-phase Zou-He velocity inlet / pressure outlet of
+ *      Sec. 2.5 (rotated to a west inlet and an east outlet).
+ *
+ * Conventions
+ *   - Lattice nx * ny nodes; host field arrays are double, nx*ny values,
+ *     x fastest (index y*nx + x).
+ *   - Colour red (k = 0) is the heavy phase with reference density
+ *     rho_r^0 = gamma, blue (k = 1) the light one with rho_b^0 = 1; the colour
+ *     field psi is +1 in pure red, -1 in pure blue (Eq. (eq:color_field)).
+ *   - Velocities u include the Guo half-force shift: u = (sum N c + rho g/2)/rho.
+ *   - Pressure p = sum_k rho_k (c_s^k)^2 with (c_s^k)^2 = 3 (1 - alpha_k)/5
+ *     (Eq. (eq:pressureRelation)).
+ *   - Every call returns an lbm_status; nothing throws across the ABI.  On
+ *     failure lbm_last_error() returns a message for that simulation.
+ *   - One simulation is driven by one host thread at a time.  lbm_step and
+ *     lbm_batch_step are asynchronous on the simulation's CUDA stream; the
+ *     read / diagnostic / state calls synchronise that stream.
+ *   - Device memory is owned by the library (lbm_create) or by the caller
+ *     (lbm_create_ex, e.g. a torch tensor), who must keep it alive until
+ *     lbm_destroy.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,     /* invalid argument or parameter combination */
+    LBM_ENOMEM = -2,     /* device or host allocation failed / buffer too small */
+    LBM_ECUDA = -3,      /* a CUDA runtime or driver call failed */
+    LBM_EUNSTABLE = -4,  /* non-finite values found by lbm_diagnostics */
+    LBM_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    LBM_EBUDGET = -6     /* request exceeds a memory budget */
+} lbm_status;
+
+typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
+typedef enum { LBM_EQ_STD = 0, LBM_EQ_HERMITE = 1 } lbm_equilibrium;
+/* Population storage: FP32, or 16-bit deviations from the rest state with FP32
+ * arithmetic. */
+typedef enum { LBM_F32 = 0, LBM_F16DEV = 1, LBM_BF16DEV = 2 } lbm_storage;
+/* bc_x: PERIODIC or INOUT; bc_y: PERIODIC or WALL. */
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_INOUT = 2 } lbm_bc;
+typedef enum { LBM_INLET_ALTERNATE = 0, LBM_INLET_LAYERED = 1 } lbm_inlet_mode;
+/* Kernel choice: the fused single-pass kernel (default) or the two-pass
+ * reference kernel pair (moments pass + collide pass, with a scratch field). */
+typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_FUSED = 1, LBM_KERNEL_TWOPASS = 2 } lbm_kernel;
+
+typedef struct {
+    double gamma;        /* density ratio rho_r^0 / rho_b^0 >= 1 (Eq. (eq:gammaAlphaBeta)) */
+    double alpha_b;      /* rest fraction of blue, 0 < alpha_b < 1 (paper: 0.2); alpha_r =
+                            1 - (1 - alpha_b)/gamma */
+    double tau_r, tau_b; /* relaxation times, omega_k = 1/tau_k, tau_k = 3 nu_k + 1/2 */
+    double delta;        /* omega_eff interpolation half-width (paper: 0.1) */
+    double sigma;        /* surface tension (lattice units) */
+    double beta;         /* recolouring parameter in [0, 1] (paper default 0.99) */
+    double gx, gy;       /* body acceleration g (Guo forcing, F^k = rho_k g) */
+    int collision;       /* lbm_collision */
+    int equilibrium;     /* lbm_equilibrium; HERMITE adds U^k when collision == MRT */
+    double mrt_lambda;   /* s_0..s_6 = lambda omega_eff, s_7 = s_8 = omega_eff (paper: 4/5) */
+    double c7_sign;      /* sign of the d_y Q_y term of C^k_7 (+1 as printed) */
+    int bc_x;            /* LBM_BC_PERIODIC or LBM_BC_INOUT */
+    int bc_y;            /* LBM_BC_PERIODIC or LBM_BC_WALL */
+    int storage;         /* lbm_storage */
+    double u_in_r, u_in_b; /* inlet speed of the red / blue phase (bc_x == INOUT) */
+    double p_out;        /* outlet pressure (bc_x == INOUT) */
+    int inlet_mode;      /* lbm_inlet_mode */
+    int inlet_period_r, inlet_period_b; /* ALTERNATE: steps of red, then blue injection */
+    int inlet_layer;     /* LAYERED: rows y < inlet_layer inject red, the rest blue */
+    int kernel;          /* lbm_kernel */
+} lbm_params;
+
+/* FP64 diagnostics of the state at the current time t (sums over all nodes). */
+typedef struct {
+    long long t;          /* time step of the state */
+    double mass_r, mass_b;/* sum rho_r, sum rho_b */
+    double mom_x, mom_y;  /* sum rho u */
+    double max_u;         /* max |u| */
+    double area_b;        /* sum (1 - psi)/2: light-phase area */
+    double cx_b, cy_b;    /* light-phase centroid (area-weighted, unwrapped coordinates) */
+    double ux_b, ux_r;    /* area-weighted mean x-velocity of the light / heavy phase */
+    double r_eff;         /* sqrt(area_b / pi) */
+    double p_in, p_out;   /* mean p over r < r_eff/2 and over r > r_eff + 8 around the
+                             bubble centre given to lbm_init_bubble (else the centroid) */
+    double dp;            /* p_in - p_out (Laplace pressure jump) */
+    long long nonfinite;  /* nodes with a non-finite density or velocity */
+} lbm_diag;
+
+typedef struct lbm_sim lbm_sim;
+typedef struct lbm_batch lbm_batch;
+
+/* Fill *p with the paper's defaults: gamma 1, alpha_b 0.2, tau 1, delta 0.1,
+ * sigma 0.005, beta 0.99, BGK, standard equilibrium, lambda 4/5, periodic. */
+lbm_status lbm_default_params(lbm_params *p);
+
+/* Device bytes one simulation needs (both population buffers).  0 on invalid
+ * arguments. */
+size_t lbm_bytes_required(int nx, int ny, const lbm_params *p);
+
+/* Create a simulation of nx * ny nodes (nx >= 8, ny >= 4) on the current CUDA
+ * device, allocating its population buffers and a private stream.  The state
+ * is zero until an init call. */
+lbm_status lbm_create(int nx, int ny, const lbm_params *p, lbm_sim **out);
+
+/* As lbm_create, on caller-owned device memory dev_buf of at least
+ * lbm_bytes_required() bytes (256-byte aligned) and the caller's stream
+ * (cudaStream_t, may be NULL for the legacy default stream). */
+lbm_status lbm_create_ex(int nx, int ny, const lbm_params *p, void *dev_buf, size_t bytes,
+                         void *cuda_stream, lbm_sim **out);
+
+/* Sharp-interface static bubble at rest: light phase (rho_b = 1) where the
+ * periodic distance to (cx, cy) is below R, heavy phase (rho_r = gamma)
+ * elsewhere; equilibrium populations; t = 0. */
+lbm_status lbm_init_bubble(lbm_sim *s, double cx, double cy, double R);
+
+/* Periodic slug train: n_bubbles evenly spaced light stadium bubbles of length
+ * bubble_len and height bubble_h centred in y, heavy liquid elsewhere; with
+ * poiseuille != 0 the start velocity is u_x(y) = gx/(2 nu_r) Y (ny - Y),
+ * Y = y + 1/2 (Sec. 5.1); t = 0. */
+lbm_status lbm_init_slug(lbm_sim *s, int n_bubbles, double bubble_len, double bubble_h,
+                         int poiseuille);
+
+/* Equilibrium state from host fields rho_r, rho_b, ux, uy (nx*ny doubles each);
+ * t = 0. */
+lbm_status lbm_init_fields(lbm_sim *s, const double *rho_r, const double *rho_b,
+                           const double *ux, const double *uy);
+
+/* Advance n >= 0 time steps (asynchronous on the simulation's stream). */
+lbm_status lbm_step(lbm_sim *s, long n);
+
+/* Block until the simulation's queued work is done; reports CUDA errors. */
+lbm_status lbm_synchronize(lbm_sim *s);
+
+/* Current time step. */
+long long lbm_time(const lbm_sim *s);
+
+/* Macroscopic fields at the current time into caller-owned host arrays of
+ * nx*ny doubles (x fastest); any pointer may be NULL.  Synchronous. */
+lbm_status lbm_read_fields(lbm_sim *s, double *rho_r, double *rho_b, double *ux, double *uy,
+                           double *p);
+
+/* FP64 diagnostics of the current state.  Returns LBM_EUNSTABLE (with *out
+ * filled) if any node is non-finite.  Synchronous. */
+lbm_status lbm_diagnostics(lbm_sim *s, lbm_diag *out);
+
+/* Raw state (both population buffers and the time step): size, save to a
+ * host buffer, restore from one.  Synchronous.  A restored state continues
+ * bit-identically. */
+size_t lbm_state_bytes(const lbm_sim *s);
+lbm_status lbm_save_state(lbm_sim *s, void *host, size_t bytes);
+lbm_status lbm_load_state(lbm_sim *s, const void *host, size_t bytes);
+
+/* Message of the last failed call on s (or of the last failed create when s is
+ * NULL); never NULL. */
+const char *lbm_last_error(const lbm_sim *s);
+
+/* Free the simulation (its own buffers and stream; never caller memory). */
+void lbm_destroy(lbm_sim *s);
+
+/* ---- batched stepping of many independent simulations ---- */
+
+/* Group n simulations (created on the same device, any sizes and parameters,
+ * FP32 or 16-bit storage) so that lbm_batch_step advances all of them with one
+ * kernel launch per time step on the stream of sims[0].  rows_per_item > 0
+ * fixes the number of lattice rows each thread block marches over; 0 picks it
+ * from the built-in size-class table.  The simulations stay owned by the
+ * caller and must outlive the batch. */
+lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out);
+
+/* Advance every simulation of the batch by n steps; with use_graph != 0 the
+ * launches are captured once into a CUDA graph of n steps and replayed on
+ * later calls with the same n. Asynchronous. */
+lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph);
+
+/* Number of work items (thread blocks) of one batched step. */
+int lbm_batch_items(const lbm_batch *b);
+
+void lbm_batch_destroy(lbm_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -32,9 +32,10 @@
  *     term each), as Eq. (eq:perturbation) is printed;
  *   - the recolouring term is zero when i = 0 or |F| == 0 exactly;
  *   - Guo-Zheng-Shi forcing with F^k = rho_k g and u = (sum N c + rho g / 2) / rho;
- *   - halfway bounce-back; psi on a node outside the domain is the
- *     W-weighted mean of its in-domain neighbours (the wetting extrapolation of
- *     Sec. 2.4 without the stray c_{i alpha} factor);
+ *   - halfway bounce-back; psi on a solid node is the W-weighted mean of its
+ *     in-domain neighbours (the wetting extrapolation of Sec. 2.4 without the
+ *     stray c_{i alpha} factor); behind an open inlet / outlet psi and Q^k are
+ *     copied from the boundary node (zero normal gradient), Q^k = 0 in walls;
  *   - the paper's north inlet / south outlet are rotated to a west inlet /
  *     east outlet; the inlet phase is prescribed, the outlet colour fraction
  *     comes from the known populations, the outlet velocity is
@@ -484,11 +485,18 @@ static int in_domain(const orc_params *p, int X, int Y, int *xw, int *yw) {
     return 1;
 }
 
-/* psi at any lattice position next to the domain (Sec. 2.4 extrapolation for
- * nodes outside the domain). */
+/* psi at any lattice position next to the domain.  Behind a no-slip wall
+ * (a solid node) it is the W-weighted mean of the in-domain neighbours
+ * (Sec. 2.4 extrapolation); behind an open inlet / outlet column it is the
+ * value of the boundary node on the same row (zero normal gradient). */
 static double psi_at(const orc_sim *s, int X, int Y) {
     int xw, yw;
     if (in_domain(&s->p, X, Y, &xw, &yw)) return s->psi[(size_t)yw * s->p.nx + xw];
+    int out_y = (Y < 0 || Y >= s->p.ny);
+    if (!out_y && s->p.bc_x == ORC_INOUT) {
+        int xc = X < 0 ? 0 : s->p.nx - 1;
+        return s->psi[(size_t)Y * s->p.nx + xc];
+    }
     double num = 0.0, den = 0.0;
     for (int i = 1; i < 9; i++)
         if (in_domain(&s->p, X + CX[i], Y + CY[i], &xw, &yw)) {
@@ -499,22 +507,19 @@ static double psi_at(const orc_sim *s, int X, int Y) {
 }
 
 /* Q^k (component comp: 0 x, 1 y) at any lattice position next to the domain:
- * zero behind a no-slip wall, extrapolated like psi behind an inlet/outlet. */
+ * zero behind a no-slip wall (u = 0 there), the boundary node's value behind
+ * an open inlet / outlet column (zero normal gradient). */
 static double Q_at(const orc_sim *s, int k, int comp, int X, int Y) {
     const double *Q = comp == 0 ? s->Qx : s->Qy;
     size_t n = (size_t)s->p.nx * s->p.ny;
     int xw, yw;
     if (in_domain(&s->p, X, Y, &xw, &yw)) return Q[k * n + (size_t)yw * s->p.nx + xw];
     int out_y = (Y < 0 || Y >= s->p.ny);
-    int out_x = (X < 0 || X >= s->p.nx);
-    if ((out_y && s->p.bc_y == ORC_WALL) || (out_x && s->p.bc_x == ORC_WALL)) return 0.0;
-    double num = 0.0, den = 0.0;
-    for (int i = 1; i < 9; i++)
-        if (in_domain(&s->p, X + CX[i], Y + CY[i], &xw, &yw)) {
-            num += W(i) * Q[k * n + (size_t)yw * s->p.nx + xw];
-            den += W(i);
-        }
-    return den > 0.0 ? num / den : 0.0;
+    if (!out_y && s->p.bc_x == ORC_INOUT) {
+        int xc = X < 0 ? 0 : s->p.nx - 1;
+        return Q[k * n + (size_t)Y * s->p.nx + xc];
+    }
+    return 0.0;
 }
 
 /* Moments, colour field and Q^k of every node of the current state. */
