@@ -1,0 +1,808 @@
+// lbm_api.cu -- host implementation of the C ABI declared in include/lbm.h.
+//
+// Owns parameters, device buffers, streams, TMA descriptors, work tables,
+// CUDA graphs and error reporting.  All lattice arithmetic runs in the kernels
+// of lbm_kernels.cuh; the host only derives the per-simulation constants of
+// arXiv 1903.01168 Sec. 2.1 (alpha_r from gamma, the omega_eff interpolation
+// coefficients, A / omega_eff = 9 sigma / 4) and lays out the geometry of the
+// initial states.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int FUSED_W = 128;     // columns per strip = threads per block
+constexpr int FUSED_NSLOT = 6;   // shared-memory row slots per block
+
+thread_local char g_create_err[256] = "";
+
+void set_err(char *buf, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 256, fmt, ap);
+    va_end(ap);
+}
+
+int elem_size(int storage) { return storage == ST_F32 ? 4 : 2; }
+
+// ---- driver entry point for tensor-map encoding (no -lcuda link needed)
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <typename T>
+const void *fused_kernel_ptr() {
+    return reinterpret_cast<const void *>(&k_step_fused<T, FUSED_W, FUSED_NSLOT>);
+}
+
+template <typename T>
+int fused_smem() {
+    return FusedCfg<T, FUSED_W, FUSED_NSLOT>::SMEM;
+}
+
+}  // namespace
+
+struct lbm_sim {
+    int dev = 0;
+    int nx = 0, ny = 0;
+    lbm_params p{};
+    SimDesc h{};                 // host copy of the descriptor
+    SimDesc *d_desc = nullptr;   // device copy
+    void *pop = nullptr;
+    size_t pop_bytes = 0;
+    bool own_pop = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    long long t = 0;
+    long long dev_t0 = -1;       // t0 last written into d_desc
+    WorkItem *d_items = nullptr;
+    int n_items = 0;
+    int *d_err = nullptr;
+    float *d_aux = nullptr;      // two-pass scratch field
+    double *d_part = nullptr;    // diagnostic partials + final
+    int diag_blocks = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    bool has_center = false;
+    double cx = 0.0, cy = 0.0;
+    char err[256] = "";
+};
+
+struct lbm_batch {
+    std::vector<lbm_sim *> sims;
+    std::vector<long long> t_mirror;  // t0 of each batch descriptor as last written
+    SimDesc *d_descs = nullptr;
+    WorkItem *d_items = nullptr;
+    int n_items = 0;
+    int storage = 0;
+    int *d_err = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    long graph_steps = 0;
+};
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_err(s->err, "%s failed: %s", #call, cudaGetErrorString(e_));              \
+            return LBM_ECUDA;                                                             \
+        }                                                                                 \
+    } while (0)
+
+namespace {
+
+lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
+    if (!p) { set_err(err, "params is NULL"); return LBM_EINVAL; }
+    if (nx < 8 || ny < 4 || nx > (1 << 24) || ny > (1 << 24)) {
+        set_err(err, "lattice %dx%d out of range (nx >= 8, ny >= 4)", nx, ny);
+        return LBM_EINVAL;
+    }
+    if (!(p->gamma >= 1.0) || !(p->alpha_b > 0.0 && p->alpha_b < 1.0)) {
+        set_err(err, "need gamma >= 1 and 0 < alpha_b < 1");
+        return LBM_EINVAL;
+    }
+    if (!(p->tau_r > 0.5) || !(p->tau_b > 0.5) || !(p->delta > 0.0)) {
+        set_err(err, "need tau_r, tau_b > 1/2 and delta > 0");
+        return LBM_EINVAL;
+    }
+    if (!(p->beta >= 0.0 && p->beta <= 1.0) || !(p->sigma >= 0.0)) {
+        set_err(err, "need 0 <= beta <= 1 and sigma >= 0");
+        return LBM_EINVAL;
+    }
+    if (p->collision < 0 || p->collision > 1 || p->equilibrium < 0 || p->equilibrium > 1) {
+        set_err(err, "unknown collision / equilibrium");
+        return LBM_EINVAL;
+    }
+    if (!(p->bc_x == LBM_BC_PERIODIC || p->bc_x == LBM_BC_INOUT) ||
+        !(p->bc_y == LBM_BC_PERIODIC || p->bc_y == LBM_BC_WALL)) {
+        set_err(err, "bc_x must be PERIODIC or INOUT, bc_y PERIODIC or WALL");
+        return LBM_EINVAL;
+    }
+    if (p->storage < 0 || p->storage > 2) { set_err(err, "unknown storage"); return LBM_EINVAL; }
+    if (p->kernel < 0 || p->kernel > 2) { set_err(err, "unknown kernel"); return LBM_EINVAL; }
+    if (p->bc_x == LBM_BC_INOUT && !(p->p_out > 0.0)) {
+        set_err(err, "inlet/outlet needs p_out > 0");
+        return LBM_EINVAL;
+    }
+    return LBM_OK;
+}
+
+int ghost_of(int storage) { return 16 / elem_size(storage); }
+
+int pitch_of(int nx, int storage) {
+    const int g = ghost_of(storage);
+    const int align = 16 / elem_size(storage);          // 16-byte row stride
+    return (nx + 2 * g + align - 1) / align * align;
+}
+
+// Per-simulation constants of Sec. 2.1 in the descriptor (float).
+void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
+    memset(&h, 0, sizeof(h));
+    h.nx = nx;
+    h.ny = ny;
+    h.storage = p->storage;
+    h.ghost = ghost_of(p->storage);
+    h.pitch = pitch_of(nx, p->storage);
+    h.plane_stride = (long long)ny * h.pitch;
+    h.buf_stride = 18LL * h.plane_stride;
+    h.collision = p->collision;
+    h.equilibrium = p->equilibrium;
+    h.bc_x = p->bc_x;
+    h.bc_y = p->bc_y;
+    h.inlet_mode = p->inlet_mode;
+    h.inlet_period_r = p->inlet_period_r;
+    h.inlet_period_b = p->inlet_period_b;
+    h.inlet_layer = p->inlet_layer;
+    const double alpha_b = p->alpha_b;
+    const double alpha_r = 1.0 - (1.0 - alpha_b) / p->gamma;     // Eq. (eq:gammaAlphaBeta)
+    const double wr = 1.0 / p->tau_r, wb = 1.0 / p->tau_b;
+    const double chi = 2.0 * wr * wb / (wr + wb);
+    const double eta = 2.0 * (wr - chi) / p->delta;
+    const double lam = 2.0 * (chi - wb) / p->delta;
+    h.inv_gamma = (float)(1.0 / p->gamma);
+    const double ar[3] = {alpha_r, (1.0 - alpha_r) / 5.0, (1.0 - alpha_r) / 20.0};
+    const double ab[3] = {alpha_b, (1.0 - alpha_b) / 5.0, (1.0 - alpha_b) / 20.0};
+    for (int c = 0; c < 3; c++) {
+        h.phi_r[c] = (float)ar[c];
+        h.phi_b[c] = (float)ab[c];
+    }
+    h.omega_r = (float)wr;
+    h.omega_b = (float)wb;
+    h.chi = (float)chi;
+    h.eta = (float)eta;
+    h.kappa = (float)(-eta / (2.0 * p->delta));
+    h.lam = (float)lam;
+    h.nu = (float)(lam / (2.0 * p->delta));
+    h.delta = (float)p->delta;
+    h.a_coef = (float)(9.0 * p->sigma / 4.0);                     // Eq. (eq:sigmaIsoAllen)
+    h.beta = (float)p->beta;
+    h.gx = (float)p->gx;
+    h.gy = (float)p->gy;
+    h.mrt_lambda = (float)p->mrt_lambda;
+    h.c7 = (float)p->c7_sign;
+    const double cs2_r = 3.0 * (1.0 - alpha_r) / 5.0, cs2_b = 3.0 * (1.0 - alpha_b) / 5.0;
+    h.cs2_r = (float)cs2_r;
+    h.cs2_b = (float)cs2_b;
+    h.herm_r = (float)(3.0 * cs2_r - 1.0);
+    h.herm_b = (float)(3.0 * cs2_b - 1.0);
+    h.q_r = (float)(1.8 * alpha_r - 0.8);
+    h.q_b = (float)(1.8 * alpha_b - 0.8);
+    h.u_in_r = (float)p->u_in_r;
+    h.u_in_b = (float)p->u_in_b;
+    h.p_out = (float)p->p_out;
+    // 16-bit storage keeps deviations from the rest state of each colour's
+    // own bulk phase, rho_k^0 phi^k_i; FP32 storage keeps N itself.
+    for (int k = 0; k < 2; k++)
+        for (int i = 0; i < 9; i++) {
+            const int c2 = C2(i);
+            const double rho0 = k == 0 ? p->gamma : 1.0;
+            h.ref[k * 9 + i] = p->storage == ST_F32 ? 0.0f : (float)(rho0 * (k == 0 ? ar[c2] : ab[c2]));
+        }
+}
+
+lbm_status encode_tmap(lbm_sim *s) {
+    auto enc = get_encode();
+    if (!enc) { set_err(s->err, "cuTensorMapEncodeTiled entry point not available"); return LBM_ECUDA; }
+    const int es = elem_size(s->p.storage);
+    const CUtensorMapDataType dt = s->p.storage == ST_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : s->p.storage == ST_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const int box_w = FUSED_W + 2 * s->h.ghost;
+    cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch, (cuuint64_t)s->ny, 36};
+    cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch * es, (cuuint64_t)s->h.plane_stride * es};
+    cuuint32_t box[3] = {(cuuint32_t)box_w, 1, 18};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&s->h.tmap, dt, 3, s->pop, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_err(s->err, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return LBM_ECUDA;
+    }
+    return LBM_OK;
+}
+
+// Rows each block marches over for a lattice of `strip_rows` strip-rows in total.
+int default_rows_per_item(long long strip_rows, int ny) {
+    const long long target = 152LL * 3 * 2;                 // ~two waves of resident blocks
+    long long L = (strip_rows + target - 1) / target;
+    L = std::max<long long>(L, 8);
+    L = std::min<long long>(L, 64);
+    return (int)std::min<long long>(L, ny);
+}
+
+void build_items(std::vector<WorkItem> &out, int sim, int nx, int ny, int L) {
+    for (int x0 = 0; x0 < nx; x0 += FUSED_W) {
+        const int w = std::min(FUSED_W, nx - x0);
+        for (int ya = 0; ya < ny; ya += L) {
+            WorkItem it{};
+            it.sim = sim;
+            it.x0 = x0;
+            it.w = w;
+            it.ya = ya;
+            it.yb = std::min(ny, ya + L);
+            out.push_back(it);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_fused(const SimDesc *descs, const WorkItem *items, int n_items, int off, int *err,
+                         cudaStream_t st) {
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_done[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel_ptr<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             fused_smem<T>());
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    k_step_fused<T, FUSED_W, FUSED_NSLOT><<<n_items, FUSED_W, fused_smem<T>(), st>>>(descs, items, n_items, off, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_any(int storage, const SimDesc *descs, const WorkItem *items, int n_items, int off,
+                             int *err, cudaStream_t st) {
+    switch (storage) {
+    case ST_F32: return launch_fused<float>(descs, items, n_items, off, err, st);
+    case ST_F16DEV: return launch_fused<__half>(descs, items, n_items, off, err, st);
+    default: return launch_fused<__nv_bfloat16>(descs, items, n_items, off, err, st);
+    }
+}
+
+int grid_for(long long n, int threads) {
+    long long g = (n + threads - 1) / threads;
+    return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
+}
+
+template <typename T>
+cudaError_t launch_twopass(lbm_sim *s, int off_t) {
+    const long long n = (long long)s->nx * s->ny;
+    const long long t = s->t + off_t;
+    const int g = grid_for(n, 256);
+    k_tp_moments<T><<<g, 256, 0, s->stream>>>(s->d_desc, t, s->d_aux);
+    k_tp_collide<T><<<g, 256, 0, s->stream>>>(s->d_desc, t, s->d_aux);
+    return cudaGetLastError();
+}
+
+bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS; }
+
+lbm_status sync_t0(lbm_sim *s) {
+    if (s->dev_t0 != s->t) {
+        k_set_t0<<<1, 32, 0, s->stream>>>(s->d_desc, s->t);
+        CK(cudaGetLastError());
+        s->dev_t0 = s->t;
+    }
+    return LBM_OK;
+}
+
+lbm_status check_err_word(lbm_sim *s, int *d_err) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (h & ERR_TIMEOUT) { set_err(s->err, "a bounded device wait timed out"); return LBM_ETIMEOUT; }
+    if (h & ERR_BADITEM) { set_err(s->err, "invalid work item"); return LBM_EINVAL; }
+    return LBM_OK;
+}
+
+// Launch `n` steps of a single simulation directly (no graph).
+lbm_status step_direct(lbm_sim *s, long n) {
+    for (long j = 0; j < n; j++) {
+        if (use_fused(s)) {
+            CK(launch_fused_any(s->p.storage, s->d_desc, s->d_items, s->n_items, (int)j, s->d_err, s->stream));
+        } else {
+            cudaError_t e = s->p.storage == ST_F32 ? launch_twopass<float>(s, (int)j)
+                            : s->p.storage == ST_F16DEV ? launch_twopass<__half>(s, (int)j)
+                                                        : launch_twopass<__nv_bfloat16>(s, (int)j);
+            CK(e);
+        }
+    }
+    k_advance<<<1, 32, 0, s->stream>>>(s->d_desc, 1, n);
+    CK(cudaGetLastError());
+    return LBM_OK;
+}
+
+constexpr int GRAPH_CHUNK = 32;
+
+lbm_status set_fields_from_host(lbm_sim *s, const double *rr, const double *rb, const double *ux,
+                                const double *uy) {
+    const size_t n = (size_t)s->nx * s->ny;
+    double *d = nullptr;
+    CK(cudaMallocAsync(&d, 4 * n * sizeof(double), s->stream));
+    CK(cudaMemcpyAsync(d, rr, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(d + n, rb, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(d + 2 * n, ux, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(d + 3 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemsetAsync(s->pop, 0, s->pop_bytes, s->stream));
+    s->t = 0;
+    lbm_status st = sync_t0(s);
+    if (st != LBM_OK) return st;
+    const int g = grid_for((long long)n, 256);
+    switch (s->p.storage) {
+    case ST_F32: k_init<float><<<g, 256, 0, s->stream>>>(s->d_desc, d, d + n, d + 2 * n, d + 3 * n); break;
+    case ST_F16DEV: k_init<__half><<<g, 256, 0, s->stream>>>(s->d_desc, d, d + n, d + 2 * n, d + 3 * n); break;
+    default: k_init<__nv_bfloat16><<<g, 256, 0, s->stream>>>(s->d_desc, d, d + n, d + 2 * n, d + 3 * n); break;
+    }
+    CK(cudaGetLastError());
+    CK(cudaFreeAsync(d, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t bytes, void *stream,
+                         bool external, lbm_sim **out) {
+    if (!out) { set_err(g_create_err, "out is NULL"); return LBM_EINVAL; }
+    *out = nullptr;
+    lbm_status v = validate(nx, ny, p, g_create_err);
+    if (v != LBM_OK) return v;
+    lbm_sim *s = new lbm_sim();
+    s->nx = nx;
+    s->ny = ny;
+    s->p = *p;
+    cudaGetDevice(&s->dev);
+    fill_desc(s->h, nx, ny, p);
+    s->pop_bytes = lbm_bytes_required(nx, ny, p);
+    auto fail = [&](lbm_status st) {
+        snprintf(g_create_err, sizeof(g_create_err), "%s", s->err);
+        lbm_destroy(s);
+        return st;
+    };
+    if (external) {
+        if (!buf || bytes < s->pop_bytes || (reinterpret_cast<uintptr_t>(buf) & 255)) {
+            set_err(s->err, "caller buffer NULL, smaller than %zu bytes or not 256-byte aligned", s->pop_bytes);
+            return fail(bytes < s->pop_bytes ? LBM_ENOMEM : LBM_EINVAL);
+        }
+        s->pop = buf;
+        s->own_pop = false;
+        s->stream = reinterpret_cast<cudaStream_t>(stream);
+        s->own_stream = false;
+    } else {
+        if (cudaMalloc(&s->pop, s->pop_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_err(s->err, "cudaMalloc of %zu bytes failed", s->pop_bytes);
+            return fail(LBM_ENOMEM);
+        }
+        s->own_pop = true;
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            set_err(s->err, "cudaStreamCreate failed");
+            return fail(LBM_ECUDA);
+        }
+        s->own_stream = true;
+    }
+    s->h.pop = s->pop;
+    if (encode_tmap(s) != LBM_OK) return fail(LBM_ECUDA);
+    if (cudaMalloc(&s->d_desc, sizeof(SimDesc)) != cudaSuccess || cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess) {
+        set_err(s->err, "cudaMalloc of descriptor failed");
+        return fail(LBM_ENOMEM);
+    }
+    std::vector<WorkItem> items;
+    const long long strips = (nx + FUSED_W - 1) / FUSED_W;
+    build_items(items, 0, nx, ny, default_rows_per_item(strips * ny, ny));
+    s->n_items = (int)items.size();
+    if (cudaMalloc(&s->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess) {
+        set_err(s->err, "cudaMalloc of work items failed");
+        return fail(LBM_ENOMEM);
+    }
+    const size_t nn = (size_t)nx * ny;
+    if (p->kernel == LBM_KERNEL_TWOPASS && cudaMalloc(&s->d_aux, 3 * nn * sizeof(float)) != cudaSuccess) {
+        set_err(s->err, "cudaMalloc of scratch field failed");
+        return fail(LBM_ENOMEM);
+    }
+    s->diag_blocks = grid_for((long long)nn, DIAG_THREADS);
+    if (cudaMalloc(&s->d_part, ((size_t)s->diag_blocks + 1) * DIAG_NQ * sizeof(double)) != cudaSuccess) {
+        set_err(s->err, "cudaMalloc of diagnostic scratch failed");
+        return fail(LBM_ENOMEM);
+    }
+    if (cudaMemcpyAsync(s->d_desc, &s->h, sizeof(SimDesc), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+        cudaMemcpyAsync(s->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) != cudaSuccess ||
+        cudaMemsetAsync(s->pop, 0, s->pop_bytes, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        set_err(s->err, "initial uploads failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(LBM_ECUDA);
+    }
+    s->dev_t0 = 0;
+    *out = s;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_default_params(lbm_params *p) {
+    if (!p) return LBM_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->gamma = 1.0;
+    p->alpha_b = 0.2;
+    p->tau_r = 1.0;
+    p->tau_b = 1.0;
+    p->delta = 0.1;
+    p->sigma = 0.005;
+    p->beta = 0.99;
+    p->mrt_lambda = 0.8;
+    p->c7_sign = 1.0;
+    return LBM_OK;
+}
+
+size_t lbm_bytes_required(int nx, int ny, const lbm_params *p) {
+    char tmp[256];
+    if (validate(nx, ny, p, tmp) != LBM_OK) return 0;
+    return 2ull * 18ull * (size_t)ny * (size_t)pitch_of(nx, p->storage) * elem_size(p->storage);
+}
+
+lbm_status lbm_create(int nx, int ny, const lbm_params *p, lbm_sim **out) {
+    return create_common(nx, ny, p, nullptr, 0, nullptr, false, out);
+}
+
+lbm_status lbm_create_ex(int nx, int ny, const lbm_params *p, void *dev_buf, size_t bytes, void *cuda_stream,
+                         lbm_sim **out) {
+    return create_common(nx, ny, p, dev_buf, bytes, cuda_stream, true, out);
+}
+
+lbm_status lbm_init_fields(lbm_sim *s, const double *rho_r, const double *rho_b, const double *ux,
+                           const double *uy) {
+    if (!s) return LBM_EINVAL;
+    if (!rho_r || !rho_b || !ux || !uy) { set_err(s->err, "NULL field"); return LBM_EINVAL; }
+    return set_fields_from_host(s, rho_r, rho_b, ux, uy);
+}
+
+lbm_status lbm_init_bubble(lbm_sim *s, double cx, double cy, double R) {
+    if (!s) return LBM_EINVAL;
+    if (!(R > 0.0)) { set_err(s->err, "R must be > 0"); return LBM_EINVAL; }
+    const int nx = s->nx, ny = s->ny;
+    std::vector<double> rr((size_t)nx * ny), rb(rr.size()), z(rr.size(), 0.0);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            double dx = std::fabs(x - cx), dy = std::fabs(y - cy);
+            if (s->p.bc_x == LBM_BC_PERIODIC) dx = std::min(dx, nx - dx);
+            if (s->p.bc_y == LBM_BC_PERIODIC) dy = std::min(dy, ny - dy);
+            const bool in = dx * dx + dy * dy < R * R;
+            rr[(size_t)y * nx + x] = in ? 0.0 : s->p.gamma;
+            rb[(size_t)y * nx + x] = in ? 1.0 : 0.0;
+        }
+    lbm_status st = set_fields_from_host(s, rr.data(), rb.data(), z.data(), z.data());
+    if (st == LBM_OK) {
+        s->has_center = true;
+        s->cx = cx;
+        s->cy = cy;
+    }
+    return st;
+}
+
+lbm_status lbm_init_slug(lbm_sim *s, int n_bubbles, double bubble_len, double bubble_h, int poiseuille) {
+    if (!s) return LBM_EINVAL;
+    if (n_bubbles < 0 || bubble_len < 0 || bubble_h < 0) { set_err(s->err, "negative slug geometry"); return LBM_EINVAL; }
+    const int nx = s->nx, ny = s->ny;
+    std::vector<double> rr((size_t)nx * ny), rb(rr.size()), ux(rr.size(), 0.0), uy(rr.size(), 0.0);
+    const double r = bubble_h / 2.0, yc = (ny - 1) / 2.0, pitch = (double)nx / std::max(n_bubbles, 1);
+    const double nu_l = (s->p.tau_r - 0.5) / 3.0;
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            bool gas = false;
+            for (int b = 0; b < n_bubbles; b++) {
+                const double x0 = b * pitch + (pitch - bubble_len) / 2.0;
+                const double xs = std::fmod(std::fmod(x - x0, (double)nx) + nx, (double)nx);
+                const double dy = y - yc;
+                const bool core = xs >= r && xs <= bubble_len - r && std::fabs(dy) < r;
+                const bool c1 = (xs - r) * (xs - r) + dy * dy < r * r;
+                const bool c2 = (xs - (bubble_len - r)) * (xs - (bubble_len - r)) + dy * dy < r * r;
+                gas = gas || core || (xs <= bubble_len && (c1 || c2));
+            }
+            const size_t k = (size_t)y * nx + x;
+            rr[k] = gas ? 0.0 : s->p.gamma;
+            rb[k] = gas ? 1.0 : 0.0;
+            if (poiseuille && s->p.gx != 0.0) {
+                const double Y = y + 0.5;
+                ux[k] = s->p.gx / (2.0 * nu_l) * Y * (ny - Y);
+            }
+        }
+    return set_fields_from_host(s, rr.data(), rb.data(), ux.data(), uy.data());
+}
+
+lbm_status lbm_step(lbm_sim *s, long n) {
+    if (!s) return LBM_EINVAL;
+    if (n < 0) { set_err(s->err, "n < 0"); return LBM_EINVAL; }
+    if (n == 0) return LBM_OK;
+    lbm_status st = sync_t0(s);
+    if (st != LBM_OK) return st;
+    long done = 0;
+    // a captured graph of GRAPH_CHUNK steps (+ time advance), replayed
+    if (n >= GRAPH_CHUNK && s->stream != nullptr) {
+        if (!s->graph) {
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            lbm_status cs = step_direct(s, GRAPH_CHUNK);
+            cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
+            if (cs != LBM_OK) return cs;
+            CK(ce);
+            CK(cudaGraphInstantiate(&s->graph, g, 0));
+            cudaGraphDestroy(g);
+            s->graph_steps = GRAPH_CHUNK;
+        }
+        for (; done + GRAPH_CHUNK <= n; done += GRAPH_CHUNK) CK(cudaGraphLaunch(s->graph, s->stream));
+    }
+    if (done < n) {
+        st = step_direct(s, n - done);
+        if (st != LBM_OK) return st;
+    }
+    s->t += n;
+    s->dev_t0 = s->t;
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_sim *s) {
+    if (!s) return LBM_EINVAL;
+    CK(cudaStreamSynchronize(s->stream));
+    return check_err_word(s, s->d_err);
+}
+
+long long lbm_time(const lbm_sim *s) { return s ? s->t : -1; }
+
+lbm_status lbm_read_fields(lbm_sim *s, double *rho_r, double *rho_b, double *ux, double *uy, double *p) {
+    if (!s) return LBM_EINVAL;
+    const size_t n = (size_t)s->nx * s->ny;
+    double *d = nullptr;
+    CK(cudaMallocAsync(&d, 5 * n * sizeof(double), s->stream));
+    const int g = grid_for((long long)n, 256);
+    switch (s->p.storage) {
+    case ST_F32: k_fields<float><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, d); break;
+    case ST_F16DEV: k_fields<__half><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, d); break;
+    default: k_fields<__nv_bfloat16><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, d); break;
+    }
+    CK(cudaGetLastError());
+    double *outs[5] = {rho_r, rho_b, ux, uy, p};
+    for (int q = 0; q < 5; q++)
+        if (outs[q]) CK(cudaMemcpyAsync(outs[q], d + q * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(d, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return check_err_word(s, s->d_err);
+}
+
+lbm_status lbm_diagnostics(lbm_sim *s, lbm_diag *out) {
+    if (!s || !out) return LBM_EINVAL;
+    memset(out, 0, sizeof(*out));
+    double h[DIAG_NQ];
+    double *fin = s->d_part + (size_t)s->diag_blocks * DIAG_NQ;
+    auto run = [&](int pass, double cx, double cy, double rin, double rout) -> lbm_status {
+        switch (s->p.storage) {
+        case ST_F32: k_diag<float><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part); break;
+        case ST_F16DEV: k_diag<__half><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part); break;
+        default: k_diag<__nv_bfloat16><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part); break;
+        }
+        CK(cudaGetLastError());
+        k_diag_final<<<1, 32, 0, s->stream>>>(s->d_part, s->diag_blocks, fin);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h, fin, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        return LBM_OK;
+    };
+    lbm_status st = run(0, 0, 0, 0, 0);
+    if (st != LBM_OK) return st;
+    out->t = s->t;
+    out->mass_r = h[0];
+    out->mass_b = h[1];
+    out->mom_x = h[2];
+    out->mom_y = h[3];
+    out->area_b = h[4];
+    out->max_u = h[5];
+    out->cx_b = h[4] > 0 ? h[6] / h[4] : 0.0;
+    out->cy_b = h[4] > 0 ? h[7] / h[4] : 0.0;
+    out->ux_b = h[4] > 0 ? h[8] / h[4] : 0.0;
+    out->ux_r = h[10] > 0 ? h[9] / h[10] : 0.0;
+    out->nonfinite = (long long)h[11];
+    out->r_eff = std::sqrt(std::max(h[4], 0.0) / M_PI);
+    const double cx = s->has_center ? s->cx : out->cx_b, cy = s->has_center ? s->cy : out->cy_b;
+    st = run(1, cx, cy, out->r_eff / 2.0, out->r_eff + 8.0);
+    if (st != LBM_OK) return st;
+    out->p_in = h[1] > 0 ? h[0] / h[1] : 0.0;
+    out->p_out = h[3] > 0 ? h[2] / h[3] : 0.0;
+    out->dp = out->p_in - out->p_out;
+    st = check_err_word(s, s->d_err);
+    if (st != LBM_OK) return st;
+    if (out->nonfinite > 0) {
+        set_err(s->err, "%lld non-finite nodes at t = %lld", out->nonfinite, s->t);
+        return LBM_EUNSTABLE;
+    }
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_sim *s) { return s ? s->pop_bytes + sizeof(long long) : 0; }
+
+lbm_status lbm_save_state(lbm_sim *s, void *host, size_t bytes) {
+    if (!s || !host) return LBM_EINVAL;
+    if (bytes < lbm_state_bytes(s)) { set_err(s->err, "state buffer too small"); return LBM_ENOMEM; }
+    memcpy(host, &s->t, sizeof(long long));
+    CK(cudaMemcpyAsync(static_cast<char *>(host) + sizeof(long long), s->pop, s->pop_bytes, cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_sim *s, const void *host, size_t bytes) {
+    if (!s || !host) return LBM_EINVAL;
+    if (bytes < lbm_state_bytes(s)) { set_err(s->err, "state buffer too small"); return LBM_ENOMEM; }
+    long long t;
+    memcpy(&t, host, sizeof(long long));
+    if (t < 0) { set_err(s->err, "corrupt state (t < 0)"); return LBM_EINVAL; }
+    CK(cudaMemcpyAsync(s->pop, static_cast<const char *>(host) + sizeof(long long), s->pop_bytes,
+                       cudaMemcpyHostToDevice, s->stream));
+    s->t = t;
+    lbm_status st = sync_t0(s);
+    if (st != LBM_OK) return st;
+    CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_sim *s) { return s ? s->err : g_create_err; }
+
+void lbm_destroy(lbm_sim *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->own_pop && s->pop) cudaFree(s->pop);
+    cudaFree(s->d_desc);
+    cudaFree(s->d_items);
+    cudaFree(s->d_err);
+    cudaFree(s->d_aux);
+    cudaFree(s->d_part);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+// ------------------------------------------------------------------ batches
+
+lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out) {
+    if (!out || !sims || n <= 0) { set_err(g_create_err, "empty batch"); return LBM_EINVAL; }
+    *out = nullptr;
+    const int storage = sims[0]->p.storage;
+    long long strip_rows = 0;
+    for (int i = 0; i < n; i++) {
+        if (!sims[i] || sims[i]->dev != sims[0]->dev || sims[i]->p.storage != storage) {
+            set_err(g_create_err, "batch members must exist, share a device and a storage type");
+            return LBM_EINVAL;
+        }
+        strip_rows += (long long)((sims[i]->nx + FUSED_W - 1) / FUSED_W) * sims[i]->ny;
+    }
+    lbm_batch *b = new lbm_batch();
+    b->sims.assign(sims, sims + n);
+    b->storage = storage;
+    b->stream = sims[0]->stream;
+    std::vector<SimDesc> descs(n);
+    std::vector<WorkItem> items;
+    for (int i = 0; i < n; i++) {
+        descs[i] = sims[i]->h;
+        descs[i].t0 = sims[i]->t;
+        b->t_mirror.push_back(sims[i]->t);
+        const int L = rows_per_item > 0 ? rows_per_item : default_rows_per_item(strip_rows, sims[i]->ny);
+        build_items(items, i, sims[i]->nx, sims[i]->ny, std::min(L, sims[i]->ny));
+    }
+    b->n_items = (int)items.size();
+    if (cudaMalloc(&b->d_descs, n * sizeof(SimDesc)) != cudaSuccess ||
+        cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess ||
+        cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(b->d_descs, descs.data(), n * sizeof(SimDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
+        set_err(g_create_err, "batch allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
+        lbm_batch_destroy(b);
+        return LBM_ENOMEM;
+    }
+    // work queued on member streams must be complete before the batch runs on sims[0]'s stream
+    for (int i = 0; i < n; i++) cudaStreamSynchronize(sims[i]->stream);
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_items(const lbm_batch *b) { return b ? b->n_items : 0; }
+
+lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
+    if (!b) return LBM_EINVAL;
+    lbm_sim *s = b->sims[0];
+    if (n < 0) { set_err(s->err, "n < 0"); return LBM_EINVAL; }
+    if (n == 0) return LBM_OK;
+    // resynchronise descriptors of members stepped outside the batch
+    for (size_t i = 0; i < b->sims.size(); i++) {
+        if (b->t_mirror[i] != b->sims[i]->t) {
+            k_set_t0<<<1, 32, 0, b->stream>>>(b->d_descs + i, b->sims[i]->t);
+            CK(cudaGetLastError());
+            b->t_mirror[i] = b->sims[i]->t;
+        }
+    }
+    const int nsims = (int)b->sims.size();
+    auto run = [&](long k) -> lbm_status {
+        for (long j = 0; j < k; j++)
+            CK(launch_fused_any(b->storage, b->d_descs, b->d_items, b->n_items, (int)j, b->d_err, b->stream));
+        k_advance<<<(nsims + 127) / 128, 128, 0, b->stream>>>(b->d_descs, nsims, k);
+        CK(cudaGetLastError());
+        return LBM_OK;
+    };
+    if (use_graph && b->stream != nullptr) {
+        if (!b->graph || b->graph_steps != n) {
+            if (b->graph) cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            lbm_status cs = run(n);
+            cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+            if (cs != LBM_OK) return cs;
+            CK(ce);
+            CK(cudaGraphInstantiate(&b->graph, g, 0));
+            cudaGraphDestroy(g);
+            b->graph_steps = n;
+        }
+        CK(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+        lbm_status st = run(n);
+        if (st != LBM_OK) return st;
+    }
+    for (size_t i = 0; i < b->sims.size(); i++) {
+        b->sims[i]->t += n;
+        b->t_mirror[i] = b->sims[i]->t;
+    }
+    // members' own streams must see the batch's work before their next call
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, b->stream));
+    for (size_t i = 1; i < b->sims.size(); i++)
+        if (b->sims[i]->stream != b->stream) CK(cudaStreamWaitEvent(b->sims[i]->stream, ev, 0));
+    cudaEventDestroy(ev);
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_err);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,270 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the
+same seeded inputs, plus bit-level consistency of the GPU paths among themselves.
+
+Tolerances (spec: relative L-infinity 1e-5 on rho and u after 100 FP32 steps):
+  rho : max_x |rho_gpu - rho_ora| / rho_ora                    <= 1e-5
+  u   : max_x |u_gpu - u_ora| / max(||u_ora||_inf, U_ref)      <= 1e-5
+U_ref is the case's velocity scale (the imposed speed for flows; the capillary
+velocity sigma / (rho nu) for static bubbles), because a relative error against
+a velocity that is itself at FP32 round-off level measures nothing."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1903_01168_gb300 import lbm as L
+from paper_1903_01168_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _native():
+    L.load(build_if_missing=True)
+
+
+def _oracle_params(nx, ny, kw):
+    ok = {k: v for k, v in kw.items() if k in O.OracleParams.__dataclass_fields__}
+    return O.OracleParams(nx=nx, ny=ny, **ok)
+
+
+def _gpu_params(kw):
+    return {k: v for k, v in kw.items() if k in L.PARAM_NAMES}
+
+
+def run_pair(nx, ny, fields, steps, kernel=L.LBM_KERNEL_FUSED, **kw):
+    o = O.Oracle(_oracle_params(nx, ny, kw))
+    o.init_fields(*fields)
+    o.step(steps)
+    fo = o.fields()
+    with L.Simulation(nx, ny, kernel=kernel, **_gpu_params(kw)) as s:
+        s.init_fields(*fields)
+        s.step(steps)
+        fg = s.fields()
+    return fo, fg
+
+
+def errors(fo, fg, u_ref):
+    rho_o = fo["rho_r"] + fo["rho_b"]
+    rho_g = fg["rho_r"] + fg["rho_b"]
+    e_rho = np.max(np.abs(rho_g - rho_o) / rho_o)
+    umax = max(np.abs(fo["ux"]).max(), np.abs(fo["uy"]).max(), u_ref)
+    e_u = max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max()) / umax
+    # colour split, relative to the local total density
+    e_col = np.max(np.abs(fg["rho_r"] - fo["rho_r"]) / rho_o)
+    return e_rho, e_u, e_col
+
+
+CASES = {
+    # name: (nx, ny, params, field recipe, u_ref)
+    "bubble64_bgk": (64, 64, dict(gamma=1.0, tau_r=1.0, tau_b=1.0, sigma=0.005, beta=0.7),
+                     lambda: W.bubble_fields(64, 64, 32, 32, 16, 1.0), 0.005 / (1.0 / 6.0)),
+    "random_ragged_mrt_hermite": (200, 37, dict(gamma=10.0, tau_r=0.6, tau_b=1.1, sigma=0.01, beta=0.7,
+                                                collision=L.LBM_MRT, equilibrium=L.LBM_EQ_HERMITE,
+                                                gx=2e-6, gy=-1e-6),
+                                  lambda: W.random_fields(200, 37, seed=11, gamma=10.0, u_amp=0.03), 0.03),
+    "walls_bgk_gravity": (136, 24, dict(gamma=5.0, tau_r=0.7, tau_b=0.9, sigma=0.005, beta=0.99,
+                                        bc_y=L.LBM_BC_WALL, gx=1e-5),
+                          lambda: W.random_fields(136, 24, seed=12, gamma=5.0, u_amp=0.02, walls_y=True), 0.02),
+    "walls_mrt_hermite": (96, 33, dict(gamma=10.0, tau_r=0.55, tau_b=1.0, sigma=0.01, beta=0.7,
+                                       collision=L.LBM_MRT, equilibrium=L.LBM_EQ_HERMITE,
+                                       bc_y=L.LBM_BC_WALL, gx=5e-6),
+                          lambda: W.random_fields(96, 33, seed=13, gamma=10.0, u_amp=0.02, walls_y=True), 0.02),
+    "inout_alternating": (160, 32, dict(gamma=5.0, tau_r=0.6, tau_b=0.6, sigma=1e-3, beta=0.7,
+                                        bc_x=L.LBM_BC_INOUT, bc_y=L.LBM_BC_WALL, u_in_r=0.0125,
+                                        u_in_b=0.075, p_out=0.48, inlet_period_r=30, inlet_period_b=20),
+                          lambda: W.slug_fields(160, 32, 5.0, 1, 40.0, 16.0), 0.075),
+    "inout_layered_hermite": (144, 20, dict(gamma=3.0, tau_r=0.7, tau_b=0.8, sigma=2e-3, beta=0.7,
+                                            collision=L.LBM_MRT, equilibrium=L.LBM_EQ_HERMITE,
+                                            bc_x=L.LBM_BC_INOUT, bc_y=L.LBM_BC_WALL, u_in_r=0.01,
+                                            u_in_b=0.06, p_out=0.5, inlet_mode=L.LBM_INLET_LAYERED,
+                                            inlet_layer=10),
+                              lambda: W.random_fields(144, 20, seed=14, gamma=3.0, u_amp=0.01, walls_y=True), 0.06),
+    "tiny_8x4": (8, 4, dict(gamma=2.0, tau_r=0.8, tau_b=0.8, sigma=0.01, beta=0.7),
+                 lambda: W.random_fields(8, 4, seed=15, gamma=2.0, n_bubbles=1, rmin=1.0, rmax=2.0, u_amp=0.02),
+                 0.02),
+    "odd_37x17_walls": (37, 17, dict(gamma=1.0, tau_r=0.9, tau_b=0.6, sigma=0.005, beta=0.7,
+                                     bc_y=L.LBM_BC_WALL, gy=-2e-6),
+                        lambda: W.random_fields(37, 17, seed=16, gamma=1.0, u_amp=0.02, walls_y=True), 0.02),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWOPASS])
+def test_parity_100_steps(name, kernel):
+    nx, ny, kw, make, u_ref = CASES[name]
+    fo, fg = run_pair(nx, ny, make(), 100, kernel=kernel, **kw)
+    e_rho, e_u, e_col = errors(fo, fg, u_ref)
+    print(f"{name} kernel={kernel}: rho {e_rho:.2e}  u {e_u:.2e}  colour {e_col:.2e}")
+    assert np.all(np.isfinite(fg["rho_r"]))
+    assert e_rho <= RTOL and e_u <= RTOL and e_col <= 10 * RTOL
+
+
+def _state_after(nx, ny, fields, steps, **kw):
+    with L.Simulation(nx, ny, **kw) as s:
+        s.init_fields(*fields)
+        s.step(steps)
+        s.synchronize()
+        return s.save_state()
+
+
+@pytest.mark.parametrize("name", ["random_ragged_mrt_hermite", "walls_mrt_hermite", "inout_alternating"])
+def test_fused_and_twopass_are_bit_identical(name):
+    nx, ny, kw, make, _ = CASES[name]
+    f = make()
+    a = _state_after(nx, ny, f, 37, kernel=L.LBM_KERNEL_FUSED, **_gpu_params(kw))
+    b = _state_after(nx, ny, f, 37, kernel=L.LBM_KERNEL_TWOPASS, **_gpu_params(kw))
+    assert a == b
+
+
+def test_graph_and_direct_stepping_agree_and_resume_is_exact():
+    nx, ny, kw, make, _ = CASES["walls_bgk_gravity"]
+    f = make()
+    with L.Simulation(nx, ny, **_gpu_params(kw)) as s:
+        s.init_fields(*f)
+        s.step(70)                     # two graph chunks + direct remainder
+        ref = s.save_state()
+    with L.Simulation(nx, ny, **_gpu_params(kw)) as s:
+        s.init_fields(*f)
+        for _ in range(7):
+            s.step(10)                 # direct launches only
+        assert s.save_state() == ref
+    with L.Simulation(nx, ny, **_gpu_params(kw)) as s:
+        s.init_fields(*f)
+        s.step(33)
+        mid = s.save_state()
+    with L.Simulation(nx, ny, **_gpu_params(kw)) as s2:
+        s2.load_state(mid)
+        assert s2.t == 33
+        s2.step(37)
+        assert s2.save_state() == ref
+
+
+def test_batch_equals_alone():
+    """Simulations of different sizes and parameters advanced in one batched launch
+    per step give bit-identical states to the same simulations advanced alone."""
+    names = ["random_ragged_mrt_hermite", "walls_bgk_gravity", "inout_alternating", "tiny_8x4"]
+    alone = []
+    for nm in names:
+        nx, ny, kw, make, _ = CASES[nm]
+        alone.append(_state_after(nx, ny, make(), 45, **_gpu_params(kw)))
+    sims = []
+    for nm in names:
+        nx, ny, kw, make, _ = CASES[nm]
+        s = L.Simulation(nx, ny, **_gpu_params(kw))
+        s.init_fields(*make())
+        sims.append(s)
+    b = L.Batch(sims, rows_per_item=8)
+    b.step(20, use_graph=True)
+    b.step(20, use_graph=True)
+    b.step(5, use_graph=False)
+    for s, ref in zip(sims, alone):
+        assert s.t == 45
+        assert s.save_state() == ref
+    b.close()
+    for s in sims:
+        s.close()
+
+
+def test_diagnostics_match_oracle_sums():
+    nx, ny, kw, make, _ = CASES["walls_mrt_hermite"]
+    f = make()
+    o = O.Oracle(_oracle_params(nx, ny, kw))
+    o.init_fields(*f)
+    o.step(60)
+    fo = o.fields()
+    with L.Simulation(nx, ny, **_gpu_params(kw)) as s:
+        s.init_fields(*f)
+        s.step(60)
+        d = s.diagnostics()
+    rho = fo["rho_r"] + fo["rho_b"]
+    assert d["t"] == 60
+    assert abs(d["mass_r"] - fo["rho_r"].sum()) <= 1e-5 * fo["rho_r"].sum()
+    assert abs(d["mass_b"] - fo["rho_b"].sum()) <= 1e-5 * fo["rho_b"].sum()
+    umax = np.hypot(fo["ux"], fo["uy"]).max()
+    assert abs(d["max_u"] - umax) <= 1e-5 * umax
+    mx = (rho * fo["ux"]).sum()
+    assert abs(d["mom_x"] - mx) <= 1e-5 * np.abs(rho * fo["ux"]).sum()
+    area = ((1 - fo["psi"]) / 2).sum()
+    assert abs(d["area_b"] - area) <= 1e-4 * area
+    assert d["nonfinite"] == 0
+
+
+def test_gpu_colour_mass_conservation_2000_steps():
+    """Per-colour mass is conserved by every operator; in FP32 the drift after
+    2000 steps stays at round-off level."""
+    with L.Simulation(64, 64, gamma=1.0, sigma=0.005, beta=0.7) as s:
+        s.init_bubble(32, 32, 16)
+        d0 = s.diagnostics()
+        s.step(2000)
+        d1 = s.diagnostics()
+    assert abs(d1["mass_r"] - d0["mass_r"]) <= 2e-5 * d0["mass_r"]
+    assert abs(d1["mass_b"] - d0["mass_b"]) <= 2e-5 * d0["mass_b"]
+
+
+def test_laplace_pressure_gpu_vs_oracle():
+    """64^2 static bubble, 2000 steps: the GPU Laplace jump matches the oracle's
+    within 1% and the Laplace law sigma / R_eff within 6%."""
+    o = _bubble_oracle()
+    fo = o.fields()
+    dp_o, R_o = W.laplace_pressure_jump(fo["p"], fo["psi"], 32, 32)
+    with L.Simulation(64, 64, gamma=1.0, tau_r=1.0, tau_b=1.0, sigma=0.005, beta=0.7) as s:
+        s.init_bubble(32, 32, 16)
+        s.step(2000)
+        d = s.diagnostics()
+    assert abs(d["dp"] - dp_o) <= 0.01 * abs(dp_o)
+    assert abs(d["r_eff"] - R_o) <= 0.01 * R_o
+    assert abs(d["dp"] * d["r_eff"] / 0.005 - 1.0) <= 0.06
+
+
+def _bubble_oracle():
+    o = O.Oracle(O.OracleParams(nx=64, ny=64, gamma=1.0, tau_r=1.0, tau_b=1.0, sigma=0.005, beta=0.7))
+    o.init_fields(*W.bubble_fields(64, 64, 32, 32, 16, 1.0))
+    o.step(2000)
+    return o
+
+
+def test_full_size_laplace_batch_sampled_parity():
+    """The launch configuration the benchmark times (the 40-run 256^2 Laplace sweep
+    as one batch, one launch per step, graph-captured): after 100 steps two
+    sampled runs match the oracle run alone at full size."""
+    specs = W.laplace_sweep(256, steps=100)
+    sims = []
+    for sp in specs:
+        s = L.Simulation(sp.nx, sp.ny, gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b, sigma=sp.sigma,
+                         beta=sp.beta)
+        s.init_bubble(*sp.bubble)
+        sims.append(s)
+    b = L.Batch(sims)
+    b.step(100, use_graph=True)
+    for idx in (3, 38):
+        sp = specs[idx]
+        o = O.Oracle(O.OracleParams(nx=256, ny=256, gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b,
+                                    sigma=sp.sigma, beta=sp.beta))
+        o.init_fields(*W.bubble_fields(256, 256, *sp.bubble, sp.gamma))
+        o.step(100)
+        fo = o.fields()
+        fg = sims[idx].fields()
+        nu = min(sp.tau_r, sp.tau_b) / 3 - 1 / 6
+        e_rho, e_u, _ = errors(fo, fg, sp.sigma / nu)
+        print(f"sweep[{idx}] rho {e_rho:.2e} u {e_u:.2e}")
+        assert e_rho <= RTOL and e_u <= RTOL
+    b.close()
+    for s in sims:
+        s.close()
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(L.LBMError) as e:
+        L.Simulation(4, 4)
+    assert e.value.status == L.LBM_EINVAL
+    with pytest.raises(L.LBMError):
+        L.Simulation(64, 64, tau_r=0.5)
+    with L.Simulation(16, 8) as s:
+        with pytest.raises(L.LBMError):
+            s.step(-1)
+        with pytest.raises(L.LBMError):
+            s.load_state(b"\0" * 8)
