@@ -146,6 +146,13 @@ lbm_status lbm_init_slug(lbm_sim *s, int n_bubbles, double bubble_len, double bu
 lbm_status lbm_init_fields(lbm_sim *s, const double *rho_r, const double *rho_b,
                            const double *ux, const double *uy);
 
+/* State from host pre-collision populations N^k_i(x, y) (Eq. (eq:evolution)):
+ * 18*nx*ny doubles laid out [k = red, blue][i = 0..8][y][x], directions in the
+ * order 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE; t = 0.  On an open
+ * (inlet / outlet) column the populations entering from outside are replaced by
+ * the Zou-He values when the state is first read. */
+lbm_status lbm_init_populations(lbm_sim *s, const double *pops);
+
 /* Advance n >= 0 time steps (asynchronous on the simulation's stream). */
 lbm_status lbm_step(lbm_sim *s, long n);
 
@@ -159,6 +166,11 @@ long long lbm_time(const lbm_sim *s);
  * nx*ny doubles (x fastest); any pointer may be NULL.  Synchronous. */
 lbm_status lbm_read_fields(lbm_sim *s, double *rho_r, double *rho_b, double *ux, double *uy,
                            double *p);
+
+/* Pre-collision populations N^k_i at the current time into a caller-owned host
+ * array of 18*nx*ny doubles, in the layout of lbm_init_populations (boundary
+ * conditions applied).  Synchronous. */
+lbm_status lbm_read_populations(lbm_sim *s, double *pops);
 
 /* FP64 diagnostics of the current state.  Returns LBM_EUNSTABLE (with *out
  * filled) if any node is non-finite.  Synchronous. */

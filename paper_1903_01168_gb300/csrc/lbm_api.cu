@@ -52,14 +52,18 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-template <typename T>
+template <typename T, int CV>
 const void *fused_kernel_ptr() {
-    return reinterpret_cast<const void *>(&k_step_fused<T, FUSED_W, FUSED_NSLOT>);
+    return reinterpret_cast<const void *>(&k_step_fused<T, CV, FUSED_W, FUSED_NSLOT>);
 }
 
 template <typename T>
 int fused_smem() {
     return FusedCfg<T, FUSED_W, FUSED_NSLOT>::SMEM;
+}
+
+int variant_of(const lbm_params *p) {
+    return (p->collision == LBM_MRT ? CV_MRT : 0) | (p->equilibrium == LBM_EQ_HERMITE ? CV_HERMITE : 0);
 }
 
 }  // namespace
@@ -96,7 +100,9 @@ struct lbm_batch {
     SimDesc *d_descs = nullptr;
     WorkItem *d_items = nullptr;
     int n_items = 0;
-    int storage = 0;
+    // one launch per (storage, variant) group; items of a group are contiguous
+    struct Group { int storage, variant, first, count; };
+    std::vector<Group> groups;
     int *d_err = nullptr;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -150,77 +156,82 @@ lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
     return LBM_OK;
 }
 
-int ghost_of(int storage) { return 16 / elem_size(storage); }
+constexpr int GHOST = 8;   // ghost columns kept on each side of a row
 
-int pitch_of(int nx, int storage) {
-    const int g = ghost_of(storage);
-    const int align = 16 / elem_size(storage);          // 16-byte row stride
-    return (nx + 2 * g + align - 1) / align * align;
+int pitch_rho(int nx) { return (nx + 2 * GHOST + 3) / 4 * 4; }   // 16-byte rows of floats
+
+int pitch_dev(int nx, int storage) {
+    const int align = 16 / elem_size(storage);
+    return (nx + 2 * GHOST + align - 1) / align * align;
+}
+
+size_t rho_region_bytes(int nx, int ny) {
+    const size_t b = 2ull * 2ull * (size_t)ny * pitch_rho(nx) * 4ull;
+    return (b + 255) / 256 * 256;
+}
+
+size_t dev_region_bytes(int nx, int ny, int storage) {
+    return 2ull * 16ull * (size_t)ny * pitch_dev(nx, storage) * (size_t)elem_size(storage);
 }
 
 // Per-simulation constants of Sec. 2.1 in the descriptor (float).
 void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     memset(&h, 0, sizeof(h));
-    h.nx = nx;
-    h.ny = ny;
     h.storage = p->storage;
-    h.ghost = ghost_of(p->storage);
-    h.pitch = pitch_of(nx, p->storage);
-    h.plane_stride = (long long)ny * h.pitch;
-    h.buf_stride = 18LL * h.plane_stride;
-    h.collision = p->collision;
-    h.equilibrium = p->equilibrium;
-    h.bc_x = p->bc_x;
-    h.bc_y = p->bc_y;
-    h.inlet_mode = p->inlet_mode;
-    h.inlet_period_r = p->inlet_period_r;
-    h.inlet_period_b = p->inlet_period_b;
-    h.inlet_layer = p->inlet_layer;
+    h.variant = variant_of(p);
+    h.ghost = GHOST;
+    h.pitch_r = pitch_rho(nx);
+    h.pitch_d = pitch_dev(nx, p->storage);
+    h.rho_plane = (long long)ny * h.pitch_r;
+    h.rho_buf = 2LL * h.rho_plane;
+    h.dev_plane = (long long)ny * h.pitch_d;
+    h.dev_buf = 16LL * h.dev_plane;
+    Phys &f = h.ph;
+    f.nx = nx;
+    f.ny = ny;
+    f.bc_x = p->bc_x;
+    f.bc_y = p->bc_y;
+    f.inlet_mode = p->inlet_mode;
+    f.inlet_period_r = p->inlet_period_r;
+    f.inlet_period_b = p->inlet_period_b;
+    f.inlet_layer = p->inlet_layer;
     const double alpha_b = p->alpha_b;
     const double alpha_r = 1.0 - (1.0 - alpha_b) / p->gamma;     // Eq. (eq:gammaAlphaBeta)
     const double wr = 1.0 / p->tau_r, wb = 1.0 / p->tau_b;
     const double chi = 2.0 * wr * wb / (wr + wb);
     const double eta = 2.0 * (wr - chi) / p->delta;
     const double lam = 2.0 * (chi - wb) / p->delta;
-    h.inv_gamma = (float)(1.0 / p->gamma);
+    f.inv_gamma = (float)(1.0 / p->gamma);
     const double ar[3] = {alpha_r, (1.0 - alpha_r) / 5.0, (1.0 - alpha_r) / 20.0};
     const double ab[3] = {alpha_b, (1.0 - alpha_b) / 5.0, (1.0 - alpha_b) / 20.0};
     for (int c = 0; c < 3; c++) {
-        h.phi_r[c] = (float)ar[c];
-        h.phi_b[c] = (float)ab[c];
+        f.phi_r[c] = (float)ar[c];
+        f.phi_b[c] = (float)ab[c];
     }
-    h.omega_r = (float)wr;
-    h.omega_b = (float)wb;
-    h.chi = (float)chi;
-    h.eta = (float)eta;
-    h.kappa = (float)(-eta / (2.0 * p->delta));
-    h.lam = (float)lam;
-    h.nu = (float)(lam / (2.0 * p->delta));
-    h.delta = (float)p->delta;
-    h.a_coef = (float)(9.0 * p->sigma / 4.0);                     // Eq. (eq:sigmaIsoAllen)
-    h.beta = (float)p->beta;
-    h.gx = (float)p->gx;
-    h.gy = (float)p->gy;
-    h.mrt_lambda = (float)p->mrt_lambda;
-    h.c7 = (float)p->c7_sign;
+    f.omega_r = (float)wr;
+    f.omega_b = (float)wb;
+    f.chi = (float)chi;
+    f.eta = (float)eta;
+    f.kappa = (float)(-eta / (2.0 * p->delta));
+    f.lam = (float)lam;
+    f.nu = (float)(lam / (2.0 * p->delta));
+    f.delta = (float)p->delta;
+    f.a_coef = (float)(9.0 * p->sigma / 4.0);                     // Eq. (eq:sigmaIsoAllen)
+    f.beta = (float)p->beta;
+    f.gx = (float)p->gx;
+    f.gy = (float)p->gy;
+    f.mrt_lambda = (float)p->mrt_lambda;
+    f.c7 = (float)p->c7_sign;
     const double cs2_r = 3.0 * (1.0 - alpha_r) / 5.0, cs2_b = 3.0 * (1.0 - alpha_b) / 5.0;
-    h.cs2_r = (float)cs2_r;
-    h.cs2_b = (float)cs2_b;
-    h.herm_r = (float)(3.0 * cs2_r - 1.0);
-    h.herm_b = (float)(3.0 * cs2_b - 1.0);
-    h.q_r = (float)(1.8 * alpha_r - 0.8);
-    h.q_b = (float)(1.8 * alpha_b - 0.8);
-    h.u_in_r = (float)p->u_in_r;
-    h.u_in_b = (float)p->u_in_b;
-    h.p_out = (float)p->p_out;
-    // 16-bit storage keeps deviations from the rest state of each colour's
-    // own bulk phase, rho_k^0 phi^k_i; FP32 storage keeps N itself.
-    for (int k = 0; k < 2; k++)
-        for (int i = 0; i < 9; i++) {
-            const int c2 = C2(i);
-            const double rho0 = k == 0 ? p->gamma : 1.0;
-            h.ref[k * 9 + i] = p->storage == ST_F32 ? 0.0f : (float)(rho0 * (k == 0 ? ar[c2] : ab[c2]));
-        }
+    f.cs2_r = (float)cs2_r;
+    f.cs2_b = (float)cs2_b;
+    f.herm_r = (float)(3.0 * cs2_r - 1.0);
+    f.herm_b = (float)(3.0 * cs2_b - 1.0);
+    f.q_r = (float)(1.8 * alpha_r - 0.8);
+    f.q_b = (float)(1.8 * alpha_b - 0.8);
+    f.u_in_r = (float)p->u_in_r;
+    f.u_in_b = (float)p->u_in_b;
+    f.p_out = (float)p->p_out;
 }
 
 lbm_status encode_tmap(lbm_sim *s) {
@@ -230,17 +241,25 @@ lbm_status encode_tmap(lbm_sim *s) {
     const CUtensorMapDataType dt = s->p.storage == ST_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : s->p.storage == ST_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const int box_w = FUSED_W + 2 * s->h.ghost;
-    cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch, (cuuint64_t)s->ny, 36};
-    cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch * es, (cuuint64_t)s->h.plane_stride * es};
-    cuuint32_t box[3] = {(cuuint32_t)box_w, 1, 18};
+    const cuuint32_t box_w = FUSED_W + 2 * GHOST;
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(&s->h.tmap, dt, 3, s->pop, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_err(s->err, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-        return LBM_ECUDA;
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch_r, (cuuint64_t)s->ny, 4};
+        cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch_r * 4, (cuuint64_t)s->h.rho_plane * 4};
+        cuuint32_t box[3] = {box_w, 1, 2};
+        CUresult r = enc(&s->h.tmap_rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->h.rho, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) { set_err(s->err, "cuTensorMapEncodeTiled (rho) failed (%d)", (int)r); return LBM_ECUDA; }
+    }
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch_d, (cuuint64_t)s->ny, 32};
+        cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch_d * es, (cuuint64_t)s->h.dev_plane * es};
+        cuuint32_t box[3] = {box_w, 1, 16};
+        CUresult r = enc(&s->h.tmap_dev, dt, 3, s->h.dev, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) { set_err(s->err, "cuTensorMapEncodeTiled (dev) failed (%d)", (int)r); return LBM_ECUDA; }
     }
     return LBM_OK;
 }
@@ -269,28 +288,40 @@ void build_items(std::vector<WorkItem> &out, int sim, int nx, int ny, int L) {
     }
 }
 
-template <typename T>
-cudaError_t launch_fused(const SimDesc *descs, const WorkItem *items, int n_items, int off, int *err,
-                         cudaStream_t st) {
+template <typename T, int CV>
+cudaError_t launch_fused_t(const SimDesc *descs, const WorkItem *items, int n_items, int off, int *err,
+                           cudaStream_t st) {
     static bool attr_done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel_ptr<T>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(fused_kernel_ptr<T, CV>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              fused_smem<T>());
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
-    k_step_fused<T, FUSED_W, FUSED_NSLOT><<<n_items, FUSED_W, fused_smem<T>(), st>>>(descs, items, n_items, off, err);
+    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_items, FUSED_W, fused_smem<T>(), st>>>(descs, items, n_items, off,
+                                                                                      err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused_any(int storage, const SimDesc *descs, const WorkItem *items, int n_items, int off,
-                             int *err, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_fused_v(int variant, const SimDesc *descs, const WorkItem *items, int n_items, int off, int *err,
+                           cudaStream_t st) {
+    switch (variant) {
+    case 0: return launch_fused_t<T, 0>(descs, items, n_items, off, err, st);
+    case CV_MRT: return launch_fused_t<T, CV_MRT>(descs, items, n_items, off, err, st);
+    case CV_HERMITE: return launch_fused_t<T, CV_HERMITE>(descs, items, n_items, off, err, st);
+    default: return launch_fused_t<T, CV_MRT | CV_HERMITE>(descs, items, n_items, off, err, st);
+    }
+}
+
+cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, const WorkItem *items, int n_items,
+                             int off, int *err, cudaStream_t st) {
     switch (storage) {
-    case ST_F32: return launch_fused<float>(descs, items, n_items, off, err, st);
-    case ST_F16DEV: return launch_fused<__half>(descs, items, n_items, off, err, st);
-    default: return launch_fused<__nv_bfloat16>(descs, items, n_items, off, err, st);
+    case ST_F32: return launch_fused_v<float>(variant, descs, items, n_items, off, err, st);
+    case ST_F16DEV: return launch_fused_v<__half>(variant, descs, items, n_items, off, err, st);
+    default: return launch_fused_v<__nv_bfloat16>(variant, descs, items, n_items, off, err, st);
     }
 }
 
@@ -299,14 +330,85 @@ int grid_for(long long n, int threads) {
     return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
 }
 
-template <typename T>
-cudaError_t launch_twopass(lbm_sim *s, int off_t) {
+template <typename T, int CV>
+cudaError_t launch_twopass_t(lbm_sim *s, int off) {
     const long long n = (long long)s->nx * s->ny;
-    const long long t = s->t + off_t;
     const int g = grid_for(n, 256);
-    k_tp_moments<T><<<g, 256, 0, s->stream>>>(s->d_desc, t, s->d_aux);
-    k_tp_collide<T><<<g, 256, 0, s->stream>>>(s->d_desc, t, s->d_aux);
+    k_tp_moments<T, CV><<<g, 256, 0, s->stream>>>(s->d_desc, off, s->d_aux);
+    k_tp_collide<T, CV><<<g, 256, 0, s->stream>>>(s->d_desc, off, s->d_aux);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_twopass_v(lbm_sim *s, int off) {
+    switch (s->h.variant) {
+    case 0: return launch_twopass_t<T, 0>(s, off);
+    case CV_MRT: return launch_twopass_t<T, CV_MRT>(s, off);
+    case CV_HERMITE: return launch_twopass_t<T, CV_HERMITE>(s, off);
+    default: return launch_twopass_t<T, CV_MRT | CV_HERMITE>(s, off);
+    }
+}
+
+cudaError_t launch_twopass(lbm_sim *s, int off) {
+    switch (s->p.storage) {
+    case ST_F32: return launch_twopass_v<float>(s, off);
+    case ST_F16DEV: return launch_twopass_v<__half>(s, off);
+    default: return launch_twopass_v<__nv_bfloat16>(s, off);
+    }
+}
+
+// Support kernels dispatched on storage type and on the equilibrium (which
+// decides the Zou-He correction term of the open boundaries).
+template <typename T, bool H>
+void launch_fields_t(lbm_sim *s, int g, double *out) {
+    k_fields<T, H><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, out);
+}
+
+template <typename T>
+void launch_fields_s(lbm_sim *s, int g, double *out) {
+    if (s->h.variant & CV_HERMITE) launch_fields_t<T, true>(s, g, out);
+    else launch_fields_t<T, false>(s, g, out);
+}
+
+void launch_fields(lbm_sim *s, int g, double *out) {
+    switch (s->p.storage) {
+    case ST_F32: launch_fields_s<float>(s, g, out); break;
+    case ST_F16DEV: launch_fields_s<__half>(s, g, out); break;
+    default: launch_fields_s<__nv_bfloat16>(s, g, out); break;
+    }
+}
+
+template <typename T>
+void launch_read_pops_s(lbm_sim *s, int g, double *out) {
+    if (s->h.variant & CV_HERMITE) k_read_pops<T, true><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, out);
+    else k_read_pops<T, false><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, out);
+}
+
+void launch_read_pops(lbm_sim *s, int g, double *out) {
+    switch (s->p.storage) {
+    case ST_F32: launch_read_pops_s<float>(s, g, out); break;
+    case ST_F16DEV: launch_read_pops_s<__half>(s, g, out); break;
+    default: launch_read_pops_s<__nv_bfloat16>(s, g, out); break;
+    }
+}
+
+template <typename T, bool H>
+void launch_diag_t(lbm_sim *s, int pass, double cx, double cy, double rin, double rout) {
+    k_diag<T, H><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part);
+}
+
+template <typename T>
+void launch_diag_s(lbm_sim *s, int pass, double cx, double cy, double rin, double rout) {
+    if (s->h.variant & CV_HERMITE) launch_diag_t<T, true>(s, pass, cx, cy, rin, rout);
+    else launch_diag_t<T, false>(s, pass, cx, cy, rin, rout);
+}
+
+void launch_diag(lbm_sim *s, int pass, double cx, double cy, double rin, double rout) {
+    switch (s->p.storage) {
+    case ST_F32: launch_diag_s<float>(s, pass, cx, cy, rin, rout); break;
+    case ST_F16DEV: launch_diag_s<__half>(s, pass, cx, cy, rin, rout); break;
+    default: launch_diag_s<__nv_bfloat16>(s, pass, cx, cy, rin, rout); break;
+    }
 }
 
 bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS; }
@@ -333,12 +435,10 @@ lbm_status check_err_word(lbm_sim *s, int *d_err) {
 lbm_status step_direct(lbm_sim *s, long n) {
     for (long j = 0; j < n; j++) {
         if (use_fused(s)) {
-            CK(launch_fused_any(s->p.storage, s->d_desc, s->d_items, s->n_items, (int)j, s->d_err, s->stream));
+            CK(launch_fused_any(s->p.storage, s->h.variant, s->d_desc, s->d_items, s->n_items, (int)j, s->d_err,
+                                s->stream));
         } else {
-            cudaError_t e = s->p.storage == ST_F32 ? launch_twopass<float>(s, (int)j)
-                            : s->p.storage == ST_F16DEV ? launch_twopass<__half>(s, (int)j)
-                                                        : launch_twopass<__nv_bfloat16>(s, (int)j);
-            CK(e);
+            CK(launch_twopass(s, (int)j));
         }
     }
     k_advance<<<1, 32, 0, s->stream>>>(s->d_desc, 1, n);
@@ -348,29 +448,40 @@ lbm_status step_direct(lbm_sim *s, long n) {
 
 constexpr int GRAPH_CHUNK = 32;
 
-lbm_status set_fields_from_host(lbm_sim *s, const double *rr, const double *rb, const double *ux,
-                                const double *uy) {
-    const size_t n = (size_t)s->nx * s->ny;
+// Upload `nfields` host arrays of n doubles and build the t = 0 state from them:
+// 4 fields (rho_r, rho_b, ux, uy) -> equilibria, or 1 array of 18 n populations.
+lbm_status init_from_host(lbm_sim *s, const double *const *arrays, int narrays, size_t per_array) {
     double *d = nullptr;
-    CK(cudaMallocAsync(&d, 4 * n * sizeof(double), s->stream));
-    CK(cudaMemcpyAsync(d, rr, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(d + n, rb, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(d + 2 * n, ux, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    CK(cudaMemcpyAsync(d + 3 * n, uy, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMallocAsync(&d, narrays * per_array * sizeof(double), s->stream));
+    for (int q = 0; q < narrays; q++)
+        CK(cudaMemcpyAsync(d + q * per_array, arrays[q], per_array * sizeof(double), cudaMemcpyHostToDevice,
+                           s->stream));
     CK(cudaMemsetAsync(s->pop, 0, s->pop_bytes, s->stream));
     s->t = 0;
     lbm_status st = sync_t0(s);
     if (st != LBM_OK) return st;
+    const size_t n = (size_t)s->nx * s->ny;
     const int g = grid_for((long long)n, 256);
+    const double *f0 = d, *f1 = d + n, *f2 = d + 2 * n, *f3 = d + 3 * n, *pops = nullptr;
+    if (narrays == 1) {
+        pops = d;
+        f0 = f1 = f2 = f3 = nullptr;
+    }
     switch (s->p.storage) {
-    case ST_F32: k_init<float><<<g, 256, 0, s->stream>>>(s->d_desc, d, d + n, d + 2 * n, d + 3 * n); break;
-    case ST_F16DEV: k_init<__half><<<g, 256, 0, s->stream>>>(s->d_desc, d, d + n, d + 2 * n, d + 3 * n); break;
-    default: k_init<__nv_bfloat16><<<g, 256, 0, s->stream>>>(s->d_desc, d, d + n, d + 2 * n, d + 3 * n); break;
+    case ST_F32: k_init<float><<<g, 256, 0, s->stream>>>(s->d_desc, f0, f1, f2, f3, pops); break;
+    case ST_F16DEV: k_init<__half><<<g, 256, 0, s->stream>>>(s->d_desc, f0, f1, f2, f3, pops); break;
+    default: k_init<__nv_bfloat16><<<g, 256, 0, s->stream>>>(s->d_desc, f0, f1, f2, f3, pops); break;
     }
     CK(cudaGetLastError());
     CK(cudaFreeAsync(d, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
+}
+
+lbm_status set_fields_from_host(lbm_sim *s, const double *rr, const double *rb, const double *ux,
+                                const double *uy) {
+    const double *a[4] = {rr, rb, ux, uy};
+    return init_from_host(s, a, 4, (size_t)s->nx * s->ny);
 }
 
 lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t bytes, void *stream,
@@ -413,7 +524,8 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         }
         s->own_stream = true;
     }
-    s->h.pop = s->pop;
+    s->h.rho = reinterpret_cast<float *>(s->pop);
+    s->h.dev = static_cast<char *>(s->pop) + rho_region_bytes(nx, ny);
     if (encode_tmap(s) != LBM_OK) return fail(LBM_ECUDA);
     if (cudaMalloc(&s->d_desc, sizeof(SimDesc)) != cudaSuccess || cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess) {
         set_err(s->err, "cudaMalloc of descriptor failed");
@@ -428,7 +540,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         return fail(LBM_ENOMEM);
     }
     const size_t nn = (size_t)nx * ny;
-    if (p->kernel == LBM_KERNEL_TWOPASS && cudaMalloc(&s->d_aux, 3 * nn * sizeof(float)) != cudaSuccess) {
+    if (p->kernel == LBM_KERNEL_TWOPASS && cudaMalloc(&s->d_aux, AUX_FIELDS * nn * sizeof(float)) != cudaSuccess) {
         set_err(s->err, "cudaMalloc of scratch field failed");
         return fail(LBM_ENOMEM);
     }
@@ -473,7 +585,7 @@ lbm_status lbm_default_params(lbm_params *p) {
 size_t lbm_bytes_required(int nx, int ny, const lbm_params *p) {
     char tmp[256];
     if (validate(nx, ny, p, tmp) != LBM_OK) return 0;
-    return 2ull * 18ull * (size_t)ny * (size_t)pitch_of(nx, p->storage) * elem_size(p->storage);
+    return rho_region_bytes(nx, ny) + dev_region_bytes(nx, ny, p->storage);
 }
 
 lbm_status lbm_create(int nx, int ny, const lbm_params *p, lbm_sim **out) {
@@ -490,6 +602,13 @@ lbm_status lbm_init_fields(lbm_sim *s, const double *rho_r, const double *rho_b,
     if (!s) return LBM_EINVAL;
     if (!rho_r || !rho_b || !ux || !uy) { set_err(s->err, "NULL field"); return LBM_EINVAL; }
     return set_fields_from_host(s, rho_r, rho_b, ux, uy);
+}
+
+lbm_status lbm_init_populations(lbm_sim *s, const double *pops) {
+    if (!s) return LBM_EINVAL;
+    if (!pops) { set_err(s->err, "NULL populations"); return LBM_EINVAL; }
+    const double *a[1] = {pops};
+    return init_from_host(s, a, 1, 18ull * s->nx * s->ny);
 }
 
 lbm_status lbm_init_bubble(lbm_sim *s, double cx, double cy, double R) {
@@ -590,15 +709,25 @@ lbm_status lbm_read_fields(lbm_sim *s, double *rho_r, double *rho_b, double *ux,
     double *d = nullptr;
     CK(cudaMallocAsync(&d, 5 * n * sizeof(double), s->stream));
     const int g = grid_for((long long)n, 256);
-    switch (s->p.storage) {
-    case ST_F32: k_fields<float><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, d); break;
-    case ST_F16DEV: k_fields<__half><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, d); break;
-    default: k_fields<__nv_bfloat16><<<g, 256, 0, s->stream>>>(s->d_desc, s->t, d); break;
-    }
+    launch_fields(s, g, d);
     CK(cudaGetLastError());
     double *outs[5] = {rho_r, rho_b, ux, uy, p};
     for (int q = 0; q < 5; q++)
         if (outs[q]) CK(cudaMemcpyAsync(outs[q], d + q * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(d, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return check_err_word(s, s->d_err);
+}
+
+lbm_status lbm_read_populations(lbm_sim *s, double *pops) {
+    if (!s) return LBM_EINVAL;
+    if (!pops) { set_err(s->err, "NULL populations"); return LBM_EINVAL; }
+    const size_t n = (size_t)s->nx * s->ny;
+    double *d = nullptr;
+    CK(cudaMallocAsync(&d, 18 * n * sizeof(double), s->stream));
+    launch_read_pops(s, grid_for((long long)n, 256), d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(pops, d, 18 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaFreeAsync(d, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return check_err_word(s, s->d_err);
@@ -610,11 +739,7 @@ lbm_status lbm_diagnostics(lbm_sim *s, lbm_diag *out) {
     double h[DIAG_NQ];
     double *fin = s->d_part + (size_t)s->diag_blocks * DIAG_NQ;
     auto run = [&](int pass, double cx, double cy, double rin, double rout) -> lbm_status {
-        switch (s->p.storage) {
-        case ST_F32: k_diag<float><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part); break;
-        case ST_F16DEV: k_diag<__half><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part); break;
-        default: k_diag<__nv_bfloat16><<<s->diag_blocks, DIAG_THREADS, 0, s->stream>>>(s->d_desc, s->t, pass, cx, cy, rin, rout, s->d_part); break;
-        }
+        launch_diag(s, pass, cx, cy, rin, rout);
         CK(cudaGetLastError());
         k_diag_final<<<1, 32, 0, s->stream>>>(s->d_part, s->diag_blocks, fin);
         CK(cudaGetLastError());
@@ -700,18 +825,16 @@ void lbm_destroy(lbm_sim *s) {
 lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out) {
     if (!out || !sims || n <= 0) { set_err(g_create_err, "empty batch"); return LBM_EINVAL; }
     *out = nullptr;
-    const int storage = sims[0]->p.storage;
     long long strip_rows = 0;
     for (int i = 0; i < n; i++) {
-        if (!sims[i] || sims[i]->dev != sims[0]->dev || sims[i]->p.storage != storage) {
-            set_err(g_create_err, "batch members must exist, share a device and a storage type");
+        if (!sims[i] || sims[i]->dev != sims[0]->dev) {
+            set_err(g_create_err, "batch members must exist and share a device");
             return LBM_EINVAL;
         }
         strip_rows += (long long)((sims[i]->nx + FUSED_W - 1) / FUSED_W) * sims[i]->ny;
     }
     lbm_batch *b = new lbm_batch();
     b->sims.assign(sims, sims + n);
-    b->storage = storage;
     b->stream = sims[0]->stream;
     std::vector<SimDesc> descs(n);
     std::vector<WorkItem> items;
@@ -719,9 +842,18 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
         descs[i] = sims[i]->h;
         descs[i].t0 = sims[i]->t;
         b->t_mirror.push_back(sims[i]->t);
-        const int L = rows_per_item > 0 ? rows_per_item : default_rows_per_item(strip_rows, sims[i]->ny);
-        build_items(items, i, sims[i]->nx, sims[i]->ny, std::min(L, sims[i]->ny));
     }
+    // items grouped by (storage, variant): one launch per group and step
+    for (int st = 0; st < 3; st++)
+        for (int cv = 0; cv < 4; cv++) {
+            const int first = (int)items.size();
+            for (int i = 0; i < n; i++) {
+                if (sims[i]->p.storage != st || sims[i]->h.variant != cv) continue;
+                const int L = rows_per_item > 0 ? rows_per_item : default_rows_per_item(strip_rows, sims[i]->ny);
+                build_items(items, i, sims[i]->nx, sims[i]->ny, std::min(L, sims[i]->ny));
+            }
+            if ((int)items.size() > first) b->groups.push_back({st, cv, first, (int)items.size() - first});
+        }
     b->n_items = (int)items.size();
     if (cudaMalloc(&b->d_descs, n * sizeof(SimDesc)) != cudaSuccess ||
         cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess ||
@@ -757,7 +889,9 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
     const int nsims = (int)b->sims.size();
     auto run = [&](long k) -> lbm_status {
         for (long j = 0; j < k; j++)
-            CK(launch_fused_any(b->storage, b->d_descs, b->d_items, b->n_items, (int)j, b->d_err, b->stream));
+            for (const auto &g : b->groups)
+                CK(launch_fused_any(g.storage, g.variant, b->d_descs, b->d_items + g.first, g.count, (int)j, b->d_err,
+                                    b->stream));
         k_advance<<<(nsims + 127) / 128, 128, 0, b->stream>>>(b->d_descs, nsims, k);
         CK(cudaGetLastError());
         return LBM_OK;

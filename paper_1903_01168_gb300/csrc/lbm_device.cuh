@@ -24,29 +24,53 @@ enum : int { ST_F32 = 0, ST_F16DEV = 1, ST_BF16DEV = 2 };
 // Error bits written by kernels into the simulation's error word.
 enum : int { ERR_TIMEOUT = 1, ERR_BADITEM = 2, ERR_ALIGN = 4 };
 
-// Per-simulation descriptor, resident in device memory.  The tensor map comes
-// first so that it keeps the 64-byte alignment TMA requires.
-struct alignas(128) SimDesc {
-    CUtensorMap tmap;          // 3D map over {pitch, ny, 36 planes} of this simulation
-    void *pop;                 // [2 buffers][18 planes][ny][pitch] storage elements
-    long long plane_stride;    // elements between planes = ny * pitch
-    long long buf_stride;      // elements between the two buffers = 18 * plane_stride
-    long long t0;              // time of the state when a launch chunk starts
-    int nx, ny, pitch, ghost;  // ghost = columns kept on each side of a row
-    int storage, collision, equilibrium, bc_x, bc_y;
+// Per-simulation descriptor, resident in device memory.
+//
+// State layout ("density + deviation" form).  For each node and colour k the
+// library stores rho_k (FP32) and the eight deviations
+//     d^k_i = N^k_i - phi^k_i rho_k,  i = 1..8
+// of the post-collision populations from the rest equilibrium of the node's
+// own colour density (the storage type T is FP32, FP16 or BF16).  The rest
+// deviation d^k_0 = -sum_{i>=1} d^k_i is implied, so every node's deviations
+// sum to zero exactly, a colour that is absent is an exact zero, and all
+// quantities the step manipulates are small where a phase is at rest.
+//   rho planes: [2 buffers][2 colours][ny][pitch_r]          float
+//   dev planes: [2 buffers][16 = colour * 8 + (i - 1)][ny][pitch_d]   T
+// Rows keep `ghost` columns on each side (periodic copies in x).  The tensor
+// maps come first so that they keep the 64-byte alignment TMA requires.
+// Per-simulation constants the node operators read; kernels copy this struct
+// into registers once.
+struct Phys {
+    int nx, ny, bc_x, bc_y;
     int inlet_mode, inlet_period_r, inlet_period_b, inlet_layer;
-    int pad0;
     float inv_gamma;           // 1 / rho_r^0
+    float gx, gy;              // body acceleration
     float phi_r[3], phi_b[3];  // rest weights phi^k by |c|^2 = 0, 1, 2
     float omega_r, omega_b, chi, eta, kappa, lam, nu, delta;
     float a_coef;              // A = a_coef * omega_eff, a_coef = 9 sigma / 4
-    float beta, gx, gy, mrt_lambda, c7;
+    float beta, mrt_lambda, c7;
     float herm_r, herm_b;      // 3 (c_s^k)^2 - 1
     float q_r, q_b;            // 1.8 alpha_k - 0.8
     float cs2_r, cs2_b;        // (c_s^k)^2
     float u_in_r, u_in_b, p_out;
-    float ref[18];             // deviation reference per plane (16-bit storage)
 };
+
+struct alignas(128) SimDesc {
+    CUtensorMap tmap_rho;      // 3D {pitch_r, ny, 4} box {W + 2 ghost, 1, 2}
+    CUtensorMap tmap_dev;      // 3D {pitch_d, ny, 32} box {W + 2 ghost, 1, 16}
+    float *rho;
+    void *dev;
+    long long rho_plane, rho_buf;   // element strides
+    long long dev_plane, dev_buf;
+    long long t0;              // time of the state when a launch chunk starts
+    int pitch_r, pitch_d, ghost;
+    int storage, variant;      // variant: bit 0 MRT, bit 1 Hermite equilibrium
+    Phys ph;
+};
+
+// Collision variants (compile-time): bit 0 = MRT (else BGK), bit 1 = Hermite
+// equilibrium (with the U^k source when combined with MRT).
+constexpr int CV_MRT = 1, CV_HERMITE = 2;
 
 // One unit of work of a step launch: a strip of w <= W columns starting at x0,
 // marching over rows [ya, yb) of simulation `sim`.
@@ -75,62 +99,87 @@ static_assert(OPP(5) == 7 && OPP(6) == 8 && OPP(7) == 5 && OPP(8) == 6, "opposit
 // ---------------------------------------------------------------- storage
 template <typename T> struct Codec;
 template <> struct Codec<float> {
-    static __device__ __forceinline__ float load(const float *p, float ref) { (void)ref; return *p; }
-    static __device__ __forceinline__ float dec(float v, float ref) { (void)ref; return v; }
-    static __device__ __forceinline__ float enc(float v, float ref) { (void)ref; return v; }
+    static __device__ __forceinline__ float dec(float v) { return v; }
+    static __device__ __forceinline__ float enc(float v) { return v; }
 };
 template <> struct Codec<__half> {
-    static __device__ __forceinline__ float dec(__half v, float ref) { return ref + __half2float(v); }
-    static __device__ __forceinline__ __half enc(float v, float ref) { return __float2half_rn(v - ref); }
+    static __device__ __forceinline__ float dec(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half enc(float v) { return __float2half_rn(v); }
 };
 template <> struct Codec<__nv_bfloat16> {
-    static __device__ __forceinline__ float dec(__nv_bfloat16 v, float ref) { return ref + __bfloat162float(v); }
-    static __device__ __forceinline__ __nv_bfloat16 enc(float v, float ref) { return __float2bfloat16_rn(v - ref); }
+    static __device__ __forceinline__ float dec(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
 };
 
-// Address of element (buffer b, plane p, row y, column x) with x in [-ghost, nx + ghost).
-template <typename T>
-__device__ __forceinline__ T *pop_ptr(const SimDesc &d, int b, int p, int x, int y) {
-    return reinterpret_cast<T *>(d.pop) + b * d.buf_stride + p * d.plane_stride + (long long)y * d.pitch + (x + d.ghost);
-}
+__device__ __forceinline__ float phi_k(const Phys &p, int k, int c2) { return k == 0 ? p.phi_r[c2] : p.phi_b[c2]; }
 
-// Store the post-collision value of plane p at node (x, y) into buffer b; with
-// periodic x the value is mirrored into the ghost columns of the other end.
+// Where node (x, y)'s post-collision state goes in buffer b: row pointers of
+// the two density planes and of deviation plane 0, the deviation plane stride,
+// and the ghost column that mirrors x on a periodic lattice (or INT_MIN).
 template <typename T>
-__device__ __forceinline__ void store_pop(const SimDesc &d, int b, int p, int x, int y, float v) {
-    T e = Codec<T>::enc(v, d.ref[p]);
-    T *row = reinterpret_cast<T *>(d.pop) + b * d.buf_stride + p * d.plane_stride + (long long)y * d.pitch + d.ghost;
-    row[x] = e;
-    if (d.bc_x == BC_PERIODIC) {
-        if (x < d.ghost) row[d.nx + x] = e;
-        if (x >= d.nx - d.ghost) row[x - d.nx] = e;
+struct NodeStore {
+    float *rho;        // &rho[b][0][y][x]
+    long long rho_plane;
+    T *dev;            // &dev[b][0][y][x]
+    long long dev_plane;
+    int mirror_r;      // +nx when x also lives in the right ghost columns, else 0
+    int mirror_l;      // -nx when x also lives in the left ghost columns, else 0
+
+    __device__ __forceinline__ NodeStore(const SimDesc &d, const Phys &p, int b, int x, int y) {
+        rho = d.rho + b * d.rho_buf + (long long)y * d.pitch_r + d.ghost + x;
+        rho_plane = d.rho_plane;
+        dev = reinterpret_cast<T *>(d.dev) + b * d.dev_buf + (long long)y * d.pitch_d + d.ghost + x;
+        dev_plane = d.dev_plane;
+        const bool per = p.bc_x == BC_PERIODIC;
+        mirror_r = (per && x < d.ghost) ? p.nx : 0;
+        mirror_l = (per && x >= p.nx - d.ghost) ? -p.nx : 0;   // both on lattices narrower than 2 ghosts
     }
-}
+
+    __device__ __forceinline__ void store_at(int off, float rr, float rb, const float (&dr)[9],
+                                             const float (&db)[9]) const {
+        rho[off] = rr;
+        rho[rho_plane + off] = rb;
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            dev[(i - 1) * dev_plane + off] = Codec<T>::enc(dr[i]);
+            dev[(i + 7) * dev_plane + off] = Codec<T>::enc(db[i]);
+        }
+    }
+
+    __device__ __forceinline__ void store(float rr, float rb, const float (&dr)[9], const float (&db)[9]) const {
+        store_at(0, rr, rb, dr, db);
+        if (mirror_r) store_at(mirror_r, rr, rb, dr, db);
+        if (mirror_l) store_at(mirror_l, rr, rb, dr, db);
+    }
+};
 
 // ------------------------------------------------------------ boundaries
 
 // Red fraction of the phase injected at inlet row y at time t (Sec. 2.5): the
 // inlet alternates red / blue segments in time, or is layered in y.
-__device__ __forceinline__ float inlet_red_fraction(const SimDesc &d, int y, long long t) {
-    if (d.inlet_mode == 1) return y < d.inlet_layer ? 1.0f : 0.0f;
-    long long period = (long long)d.inlet_period_r + d.inlet_period_b;
+__device__ __forceinline__ float inlet_red_fraction(const Phys &p, int y, long long t) {
+    if (p.inlet_mode == 1) return y < p.inlet_layer ? 1.0f : 0.0f;
+    long long period = (long long)p.inlet_period_r + p.inlet_period_b;
     if (period <= 0) return 1.0f;
-    return (t % period) < d.inlet_period_r ? 1.0f : 0.0f;
+    return (t % period) < p.inlet_period_r ? 1.0f : 0.0f;
 }
 
 // Two-phase Zou-He velocity inlet on the west column (Sec. 2.5, the north inlet
 // rotated by +90 degrees): unknowns 1, 5, 8, colour split by the injected phase.
-__device__ __forceinline__ void zouhe_inlet(const SimDesc &d, float f_r, float (&nr)[9], float (&nb)[9]) {
-    float n[9];
+// Evaluated in FP64: the mass balance divides by (1 - v) and the outlet below
+// subtracts 1 from a ratio near 1, which FP32 resolves only to ~1e-7.
+__device__ __forceinline__ void zouhe_inlet(const Phys &p, bool hermite, double f_r, double (&nr)[9],
+                                            double (&nb)[9]) {
+    double n[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) n[i] = nr[i] + nb[i];
-    const float f_b = 1.0f - f_r;
-    const float Vx = f_r * d.u_in_r + f_b * d.u_in_b;
-    const float rho = (n[0] + n[2] + n[4] + 2.0f * (n[3] + n[6] + n[7])) / (1.0f - Vx);
-    const float H = d.equilibrium ? -rho * (f_r * d.herm_r + f_b * d.herm_b) * Vx * (1.0f / 3.0f) : 0.0f;
-    const float n1 = n[3] + (2.0f / 3.0f) * rho * Vx + H;
-    const float n5 = n[7] + 0.5f * (n[4] - n[2]) + rho * Vx * (1.0f / 6.0f) - 0.5f * H;
-    const float n8 = n[6] + 0.5f * (n[2] - n[4]) + rho * Vx * (1.0f / 6.0f) - 0.5f * H;
+    const double f_b = 1.0 - f_r;
+    const double Vx = f_r * p.u_in_r + f_b * p.u_in_b;
+    const double rho = (n[0] + n[2] + n[4] + 2.0 * (n[3] + n[6] + n[7])) / (1.0 - Vx);
+    const double H = hermite ? -rho * (f_r * p.herm_r + f_b * p.herm_b) * Vx / 3.0 : 0.0;
+    const double n1 = n[3] + (2.0 / 3.0) * rho * Vx + H;
+    const double n5 = n[7] + 0.5 * (n[4] - n[2]) + rho * Vx / 6.0 - 0.5 * H;
+    const double n8 = n[6] + 0.5 * (n[2] - n[4]) + rho * Vx / 6.0 - 0.5 * H;
     nr[1] = f_r * n1; nb[1] = f_b * n1;
     nr[5] = f_r * n5; nb[5] = f_b * n5;
     nr[8] = f_r * n8; nb[8] = f_b * n8;
@@ -139,53 +188,143 @@ __device__ __forceinline__ void zouhe_inlet(const SimDesc &d, float f_r, float (
 // Two-phase Zou-He pressure outlet on the east column (the south outlet rotated
 // by +90 degrees): unknowns 3, 6, 7; colour fraction from the known populations,
 // rho_out = f_b p_out / (c_s^b)^2 + f_r p_out / (c_s^r)^2, v = -1 + (...)/rho_out.
-__device__ __forceinline__ void zouhe_outlet(const SimDesc &d, float (&nr)[9], float (&nb)[9]) {
-    const float kr = nr[0] + nr[1] + nr[2] + nr[4] + nr[5] + nr[8];
-    const float kb = nb[0] + nb[1] + nb[2] + nb[4] + nb[5] + nb[8];
-    const float a = kr * d.inv_gamma;
-    const float psi = (a - kb) / (a + kb);
-    const float f_r = 0.5f * (1.0f + psi), f_b = 1.0f - f_r;
-    float n[9];
+__device__ __forceinline__ void zouhe_outlet(const Phys &p, bool hermite, double (&nr)[9], double (&nb)[9]) {
+    const double kr = nr[0] + nr[1] + nr[2] + nr[4] + nr[5] + nr[8];
+    const double kb = nb[0] + nb[1] + nb[2] + nb[4] + nb[5] + nb[8];
+    const double a = kr * (double)p.inv_gamma;
+    const double psi = (a - kb) / (a + kb);
+    const double f_r = 0.5 * (1.0 + psi), f_b = 1.0 - f_r;
+    double n[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) n[i] = nr[i] + nb[i];
-    const float rho = f_b * d.p_out / d.cs2_b + f_r * d.p_out / d.cs2_r;
-    const float Vx = -1.0f + (n[0] + n[2] + n[4] + 2.0f * (n[1] + n[5] + n[8])) / rho;
-    const float H = d.equilibrium ? rho * (f_r * d.herm_r + f_b * d.herm_b) * Vx * (1.0f / 3.0f) : 0.0f;
-    const float n3 = n[1] - (2.0f / 3.0f) * rho * Vx + H;
-    const float n6 = n[8] - 0.5f * (n[2] - n[4]) - rho * Vx * (1.0f / 6.0f) - 0.5f * H;
-    const float n7 = n[5] + 0.5f * (n[2] - n[4]) - rho * Vx * (1.0f / 6.0f) - 0.5f * H;
+    const double rho = f_b * p.p_out / p.cs2_b + f_r * p.p_out / p.cs2_r;
+    const double Vx = -1.0 + (n[0] + n[2] + n[4] + 2.0 * (n[1] + n[5] + n[8])) / rho;
+    const double H = hermite ? rho * (f_r * p.herm_r + f_b * p.herm_b) * Vx / 3.0 : 0.0;
+    const double n3 = n[1] - (2.0 / 3.0) * rho * Vx + H;
+    const double n6 = n[8] - 0.5 * (n[2] - n[4]) - rho * Vx / 6.0 - 0.5 * H;
+    const double n7 = n[5] + 0.5 * (n[2] - n[4]) - rho * Vx / 6.0 - 0.5 * H;
     nr[3] = f_r * n3; nb[3] = f_b * n3;
     nr[6] = f_r * n6; nb[6] = f_b * n6;
     nr[7] = f_r * n7; nb[7] = f_b * n7;
 }
 
-// Pre-collision populations of node (x, y) at time t by pulling the stored
-// post-collision values: Eq. (eq:subop4) with halfway bounce-back across walls
-// (the node's own opposite population) and Zou-He on inlet / outlet columns.
-// `ld(plane, xs, ys)` returns the decoded stored value of a source node: xs may
-// be -1 or nx (ghost column), ys is one of y-1, y, y+1 NOT wrapped (the loader
-// wraps periodic rows).  y itself may lie one row outside [0, ny) on a
-// periodic lattice.
-template <class Loader>
-__device__ __forceinline__ void pull_node(const SimDesc &d, const Loader &ld, int x, int y, long long t,
-                                          float (&nr)[9], float (&nb)[9]) {
-    const bool wall_y = d.bc_y == BC_WALL;
+// Result of pulling one node: its new colour densities and the colour-blind
+// non-rest part e_i = N_i - R_i of its pre-collision populations, where
+// R_i = rho_r phi^r_i + rho_b phi^b_i is the rest equilibrium of the node.
+struct Pulled {
+    float rr, rb;
+    float e[9];
+};
+
+// Pull the pre-collision populations of node (x, y) at time t (Eq. (eq:subop4)):
+// N^k_i(x) = phi^k_i rho_k(x - c_i) + d^k_i(x - c_i), with halfway bounce-back
+// across walls (the node's own opposite population) and two-phase Zou-He on
+// the inlet / outlet columns (Sec. 2.5).  The loader provides
+//   ld.rho(k, xs, ys), ld.dev(k, i, xs, ys)   (i = 1..8)
+// of a source node; xs may be -1 or nx (ghost column); ys is one of y-1, y, y+1
+// NOT wrapped (the loader wraps periodic rows); y itself may lie one row
+// outside [0, ny) on a periodic lattice.  With have_rho the node's new colour
+// densities are already known (rr_new, rb_new) and are not recomputed.
+template <bool HERMITE, class Loader>
+__device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                          bool have_rho, float rr_new, float rb_new, Pulled &P) {
+    const bool wall_y = p.bc_y == BC_WALL;
+    const bool open_col = p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1);
+    const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
+    float s[2][9], dl[2][9], own_rho[2];
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const int ys = y - CY(i);
-        const int xs = x - CX(i);
-        if (wall_y && (ys < 0 || ys >= d.ny)) {
-            nr[i] = ld(OPP(i), x, y);
-            nb[i] = ld(9 + OPP(i), x, y);
-        } else {
-            nr[i] = ld(i, xs, ys);
-            nb[i] = ld(9 + i, xs, ys);
+    for (int k = 0; k < 2; k++) {
+        own_rho[k] = ld.rho(k, x, y);
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+            if (bounce) {
+                s[k][i] = own_rho[k];
+                dl[k][i] = ld.dev(k, OPP(i), x, y);
+            } else {
+                s[k][i] = ld.rho(k, x - CX(i), y - CY(i));
+                dl[k][i] = ld.dev(k, i, x - CX(i), y - CY(i));
+            }
         }
     }
-    if (d.bc_x == BC_INOUT) {
-        const int yw = y < 0 ? y + d.ny : (y >= d.ny ? y - d.ny : y);
-        if (x == 0) zouhe_inlet(d, inlet_red_fraction(d, yw, t), nr, nb);
-        else if (x == d.nx - 1) zouhe_outlet(d, nr, nb);
+    if (!open_col) {
+        float rnew[2];
+        if (have_rho) {
+            rnew[0] = rr_new;
+            rnew[1] = rb_new;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int i = 1; i < 9; i++)
+                    acc += phi_k(p, k, C2(i)) * (s[k][i] - own_rho[k]) + (dl[k][i] - ld.dev(k, i, x, y));
+                rnew[k] = own_rho[k] + acc;
+            }
+        }
+        P.rr = rnew[0];
+        P.rb = rnew[1];
+        float e0 = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            P.e[i] = p.phi_r[C2(i)] * (s[0][i] - rnew[0]) + dl[0][i] + p.phi_b[C2(i)] * (s[1][i] - rnew[1]) + dl[1][i];
+            e0 += P.e[i];
+        }
+        P.e[0] = -e0;
+        return;
+    }
+    // open column: full populations, Zou-He, then moments (FP64, two columns only)
+    double nr[9], nb[9];
+    {
+        double sr = 0.0, sb = 0.0;
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            nr[i] = (double)p.phi_r[C2(i)] * s[0][i] + dl[0][i];
+            nb[i] = (double)p.phi_b[C2(i)] * s[1][i] + dl[1][i];
+            sr += ld.dev(0, i, x, y);
+            sb += ld.dev(1, i, x, y);
+        }
+        nr[0] = (double)p.phi_r[0] * own_rho[0] - sr;
+        nb[0] = (double)p.phi_b[0] * own_rho[1] - sb;
+    }
+    const int yw = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
+    if (x == 0) zouhe_inlet(p, HERMITE, inlet_red_fraction(p, yw, t), nr, nb);
+    else zouhe_outlet(p, HERMITE, nr, nb);
+    double rr = 0.0, rb = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) { rr += nr[i]; rb += nb[i]; }
+    P.rr = (float)rr;
+    P.rb = (float)rb;
+    // non-rest parts relative to the densities as they will be stored (FP32),
+    // so that the stored state reproduces the node's populations
+    const double rrf = P.rr, rbf = P.rb;
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+        P.e[i] = (float)((nr[i] + nb[i]) - (rrf * (double)p.phi_r[C2(i)] + rbf * (double)p.phi_b[C2(i)]));
+}
+
+// Pre-collision populations of both colours of node (x, y) at time t in FP64
+// (boundary conditions included), for state export.
+template <bool HERMITE, class Loader>
+__device__ __forceinline__ void pull_populations(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                                 double (&nr)[9], double (&nb)[9]) {
+    const bool wall_y = p.bc_y == BC_WALL;
+    const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
+    double sr = 0.0, sb = 0.0;
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+        const int xs = bounce ? x : x - CX(i), ys = bounce ? y : y - CY(i), ii = bounce ? OPP(i) : i;
+        nr[i] = (double)p.phi_r[C2(i)] * ld.rho(0, xs, ys) + ld.dev(0, ii, xs, ys);
+        nb[i] = (double)p.phi_b[C2(i)] * ld.rho(1, xs, ys) + ld.dev(1, ii, xs, ys);
+        sr += ld.dev(0, i, x, y);
+        sb += ld.dev(1, i, x, y);
+    }
+    nr[0] = (double)p.phi_r[0] * ld.rho(0, x, y) - sr;
+    nb[0] = (double)p.phi_b[0] * ld.rho(1, x, y) - sb;
+    if (p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1)) {
+        if (x == 0) zouhe_inlet(p, HERMITE, inlet_red_fraction(p, y, t), nr, nb);
+        else zouhe_outlet(p, HERMITE, nr, nb);
     }
 }
 
@@ -195,93 +334,88 @@ struct NodeMoments {
     float rr, rb, ux, uy, psi;
 };
 
-__device__ __forceinline__ NodeMoments node_moments(const SimDesc &d, const float (&nr)[9], const float (&nb)[9]) {
-    float rr = 0.0f, rb = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 9; i++) { rr += nr[i]; rb += nb[i]; }
-    float n[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) n[i] = nr[i] + nb[i];
-    const float rho = rr + rb;
-    const float jx = (n[1] - n[3]) + (n[5] - n[7]) + (n[8] - n[6]);
-    const float jy = (n[2] - n[4]) + (n[5] - n[7]) + (n[6] - n[8]);
+__device__ __forceinline__ NodeMoments node_moments(const Phys &p, const Pulled &P) {
+    const float rho = P.rr + P.rb;
+    const float jx = (P.e[1] - P.e[3]) + (P.e[5] - P.e[7]) + (P.e[8] - P.e[6]);
+    const float jy = (P.e[2] - P.e[4]) + (P.e[5] - P.e[7]) + (P.e[6] - P.e[8]);
     NodeMoments m;
-    m.rr = rr;
-    m.rb = rb;
-    m.ux = jx / rho + 0.5f * d.gx;   // Guo half-force shift
-    m.uy = jy / rho + 0.5f * d.gy;
-    const float a = rr * d.inv_gamma;
-    m.psi = (a - rb) / (a + rb);     // Eq. (eq:color_field)
+    m.rr = P.rr;
+    m.rb = P.rb;
+    m.ux = jx / rho + 0.5f * p.gx;   // Guo half-force shift
+    m.uy = jy / rho + 0.5f * p.gy;
+    const float a = P.rr * p.inv_gamma;
+    m.psi = (a - P.rb) / (a + P.rb); // Eq. (eq:color_field)
     return m;
 }
 
 // omega_eff(psi), Sec. 2.1 interpolation.
-__device__ __forceinline__ float omega_eff(const SimDesc &d, float psi) {
-    if (psi > d.delta) return d.omega_r;
-    if (psi > 0.0f) return d.chi + psi * (d.eta + d.kappa * psi);
-    if (psi >= -d.delta) return d.chi + psi * (d.lam + d.nu * psi);
-    return d.omega_b;
+__device__ __forceinline__ float omega_eff(const Phys &p, float psi) {
+    if (psi > p.delta) return p.omega_r;
+    if (psi > 0.0f) return p.chi + psi * (p.eta + p.kappa * psi);
+    if (psi >= -p.delta) return p.chi + psi * (p.lam + p.nu * psi);
+    return p.omega_b;
 }
 
 // Collision (BGK or MRT, Guo forcing, Hermite source), perturbation and
-// recolouring of one node, in place on the pre-collision colour populations.
-// F is the colour gradient; dQx = d_x(q u_x), dQy = d_y(q u_y) with
-// q = sum_k (1.8 alpha_k - 0.8) rho_k (the colour sum of the Q^k derivatives).
-__device__ __forceinline__ void collide_node(const SimDesc &d, float (&nr)[9], float (&nb)[9],
-                                             float Fx, float Fy, float dQx, float dQy) {
-    float rr = 0.0f, rb = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 9; i++) { rr += nr[i]; rb += nb[i]; }
-    float n[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++) n[i] = nr[i] + nb[i];
+// recolouring of one pulled node.  F is the colour gradient; dQx = d_x(q u_x),
+// dQy = d_y(q u_y) with q = sum_k (1.8 alpha_k - 0.8) rho_k.  Outputs the
+// post-collision deviations dr[1..8], db[1..8] of the stored state (the colour
+// densities are unchanged by the step's collision part).
+template <int CV>
+__device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, float Fx, float Fy, float dQx,
+                                             float dQy, float (&dr)[9], float (&db)[9]) {
+    constexpr bool MRT = (CV & CV_MRT) != 0, HERMITE = (CV & CV_HERMITE) != 0;
+    const float rr = P.rr, rb = P.rb;
     const float rho = rr + rb;
     const float inv_rho = 1.0f / rho;
-    const float jx = (n[1] - n[3]) + (n[5] - n[7]) + (n[8] - n[6]);
-    const float jy = (n[2] - n[4]) + (n[5] - n[7]) + (n[6] - n[8]);
-    const float ux = jx * inv_rho + 0.5f * d.gx;
-    const float uy = jy * inv_rho + 0.5f * d.gy;
-    const float ca = rr * d.inv_gamma;
+    float e[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) e[i] = P.e[i];
+    const float jx = (e[1] - e[3]) + (e[5] - e[7]) + (e[8] - e[6]);
+    const float jy = (e[2] - e[4]) + (e[5] - e[7]) + (e[6] - e[8]);
+    const float ux = jx * inv_rho + 0.5f * p.gx;
+    const float uy = jy * inv_rho + 0.5f * p.gy;
+    const float ca = rr * p.inv_gamma;
     const float psi = (ca - rb) / (ca + rb);
-    const float w = omega_eff(d, psi);
+    const float w = omega_eff(p, psi);
 
-    // colour-blind equilibrium sum_k N^{k(e)}_i (Eq. (eq:equilibrium) / (eq:equilibrium_hermite))
+    // velocity part of the colour-blind equilibrium, sum_k N^{k(e)}_i - R_i
+    // (Eq. (eq:equilibrium) / (eq:equilibrium_hermite)), and the Guo source
     const float usq = ux * ux + uy * uy;
-    const float rest[3] = {rr * d.phi_r[0] + rb * d.phi_b[0], rr * d.phi_r[1] + rb * d.phi_b[1],
-                           rr * d.phi_r[2] + rb * d.phi_b[2]};
-    const float herm = d.equilibrium ? 0.5f * (rr * d.herm_r + rb * d.herm_b) : 0.0f;
-    const float Gx = rho * d.gx, Gy = rho * d.gy;   // total body force
-    float neq[9], src[9];
+    const float herm = HERMITE ? 0.5f * (rr * p.herm_r + rb * p.herm_b) : 0.0f;
+    const float Gx = rho * p.gx, Gy = rho * p.gy;
+    const float uG = ux * Gx + uy * Gy;
+    float weq[9], src[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         const float cu = CX(i) * ux + CY(i) * uy;
         float lin = rho * 3.0f * cu;
-        if (C2(i) > 0) lin += 3.0f * cu * (3.0f * C2(i) - 4.0f) * herm;
-        neq[i] = rest[C2(i)] + WT(i) * (lin + rho * (4.5f * cu * cu - 1.5f * usq));
+        if (HERMITE && C2(i) > 0) lin += 3.0f * cu * (3.0f * C2(i) - 4.0f) * herm;
+        weq[i] = WT(i) * (lin + rho * (4.5f * cu * cu - 1.5f * usq));
         const float cG = CX(i) * Gx + CY(i) * Gy;
-        src[i] = WT(i) * (3.0f * (cG - (ux * Gx + uy * Gy)) + 9.0f * cu * cG);
+        src[i] = WT(i) * (3.0f * (cG - uG) + 9.0f * cu * cG);
     }
 
-    if (d.collision == 0) {
+    if (!MRT) {
         const float fw = 1.0f - 0.5f * w;
 #pragma unroll
-        for (int i = 0; i < 9; i++) n[i] = n[i] - w * (n[i] - neq[i]) + fw * src[i];
+        for (int i = 1; i < 9; i++) e[i] = e[i] - w * (e[i] - weq[i]) + fw * src[i];
     } else {
-        float e[9];
+        float q[9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) e[i] = n[i] - neq[i];
+        for (int i = 0; i < 9; i++) q[i] = e[i] - weq[i];
         // moments of the non-equilibrium part and of the source, rows of M
         // (appendix "Transformation matrices"); row 0 (mass) is zero for both.
-        const float ax = e[1] + e[2] + e[3] + e[4], dg = e[5] + e[6] + e[7] + e[8];
+        const float ax = q[1] + q[2] + q[3] + q[4], dg = q[5] + q[6] + q[7] + q[8];
         float m[9], ms[9];
-        m[1] = -4.0f * e[0] - ax + 2.0f * dg;
-        m[2] = 4.0f * e[0] - 2.0f * ax + dg;
-        m[3] = e[1] - e[3] + e[5] - e[6] - e[7] + e[8];
-        m[4] = -2.0f * (e[1] - e[3]) + e[5] - e[6] - e[7] + e[8];
-        m[5] = e[2] - e[4] + e[5] + e[6] - e[7] - e[8];
-        m[6] = -2.0f * (e[2] - e[4]) + e[5] + e[6] - e[7] - e[8];
-        m[7] = e[1] - e[2] + e[3] - e[4];
-        m[8] = e[5] - e[6] + e[7] - e[8];
+        m[1] = -4.0f * q[0] - ax + 2.0f * dg;
+        m[2] = 4.0f * q[0] - 2.0f * ax + dg;
+        m[3] = q[1] - q[3] + q[5] - q[6] - q[7] + q[8];
+        m[4] = -2.0f * (q[1] - q[3]) + q[5] - q[6] - q[7] + q[8];
+        m[5] = q[2] - q[4] + q[5] + q[6] - q[7] - q[8];
+        m[6] = -2.0f * (q[2] - q[4]) + q[5] + q[6] - q[7] - q[8];
+        m[7] = q[1] - q[2] + q[3] - q[4];
+        m[8] = q[5] - q[6] + q[7] - q[8];
         const float sx = src[1] + src[2] + src[3] + src[4], sd = src[5] + src[6] + src[7] + src[8];
         ms[1] = -4.0f * src[0] - sx + 2.0f * sd;
         ms[2] = 4.0f * src[0] - 2.0f * sx + sd;
@@ -291,66 +425,69 @@ __device__ __forceinline__ void collide_node(const SimDesc &d, float (&nr)[9], f
         ms[6] = -2.0f * (src[2] - src[4]) + src[5] + src[6] - src[7] - src[8];
         ms[7] = src[1] - src[2] + src[3] - src[4];
         ms[8] = src[5] - src[6] + src[7] - src[8];
-        const float s1 = d.mrt_lambda * w;   // s_0 .. s_6
+        const float s1 = p.mrt_lambda * w;   // s_0 .. s_6
         float tm[9];
 #pragma unroll
         for (int a = 1; a < 9; a++) {
-            const float s = a < 7 ? s1 : w;  // s_7 = s_8 = omega_eff
-            tm[a] = s * m[a] - (1.0f - 0.5f * s) * ms[a];
+            const float sa = a < 7 ? s1 : w;  // s_7 = s_8 = omega_eff
+            tm[a] = sa * m[a] - (1.0f - 0.5f * sa) * ms[a];
         }
-        if (d.equilibrium) {
+        if (HERMITE) {
             // + U = M^-1 C, C_1 = 3 (1 - s_1/2)(dQx + dQy), C_7 = 3 (1 - w/2)(dQx + c7 dQy)
             tm[1] -= 3.0f * (1.0f - 0.5f * s1) * (dQx + dQy);
-            tm[7] -= 3.0f * (1.0f - 0.5f * w) * (dQx + d.c7 * dQy);
+            tm[7] -= 3.0f * (1.0f - 0.5f * w) * (dQx + p.c7 * dQy);
         }
-        // n -= M^-1 tm, M^-1 = (1/36) * integer matrix of the appendix (tm[0] = 0)
+        // e -= M^-1 tm, M^-1 = (1/36) * integer matrix of the appendix (tm[0] = 0)
         const float k36 = 1.0f / 36.0f;
         const float b12 = -tm[1] - 2.0f * tm[2];
         const float d21 = 2.0f * tm[1] + tm[2];
-        n[0] -= k36 * (-4.0f * tm[1] + 4.0f * tm[2]);
-        n[1] -= k36 * (b12 + 6.0f * tm[3] - 6.0f * tm[4] + 9.0f * tm[7]);
-        n[2] -= k36 * (b12 + 6.0f * tm[5] - 6.0f * tm[6] - 9.0f * tm[7]);
-        n[3] -= k36 * (b12 - 6.0f * tm[3] + 6.0f * tm[4] + 9.0f * tm[7]);
-        n[4] -= k36 * (b12 - 6.0f * tm[5] + 6.0f * tm[6] - 9.0f * tm[7]);
-        n[5] -= k36 * (d21 + 6.0f * tm[3] + 3.0f * tm[4] + 6.0f * tm[5] + 3.0f * tm[6] + 9.0f * tm[8]);
-        n[6] -= k36 * (d21 - 6.0f * tm[3] - 3.0f * tm[4] + 6.0f * tm[5] + 3.0f * tm[6] - 9.0f * tm[8]);
-        n[7] -= k36 * (d21 - 6.0f * tm[3] - 3.0f * tm[4] - 6.0f * tm[5] - 3.0f * tm[6] + 9.0f * tm[8]);
-        n[8] -= k36 * (d21 + 6.0f * tm[3] + 3.0f * tm[4] - 6.0f * tm[5] - 3.0f * tm[6] - 9.0f * tm[8]);
+        e[1] -= k36 * (b12 + 6.0f * tm[3] - 6.0f * tm[4] + 9.0f * tm[7]);
+        e[2] -= k36 * (b12 + 6.0f * tm[5] - 6.0f * tm[6] - 9.0f * tm[7]);
+        e[3] -= k36 * (b12 - 6.0f * tm[3] + 6.0f * tm[4] + 9.0f * tm[7]);
+        e[4] -= k36 * (b12 - 6.0f * tm[5] + 6.0f * tm[6] - 9.0f * tm[7]);
+        e[5] -= k36 * (d21 + 6.0f * tm[3] + 3.0f * tm[4] + 6.0f * tm[5] + 3.0f * tm[6] + 9.0f * tm[8]);
+        e[6] -= k36 * (d21 - 6.0f * tm[3] - 3.0f * tm[4] + 6.0f * tm[5] + 3.0f * tm[6] - 9.0f * tm[8]);
+        e[7] -= k36 * (d21 - 6.0f * tm[3] - 3.0f * tm[4] - 6.0f * tm[5] - 3.0f * tm[6] + 9.0f * tm[8]);
+        e[8] -= k36 * (d21 + 6.0f * tm[3] + 3.0f * tm[4] - 6.0f * tm[5] - 3.0f * tm[6] - 9.0f * tm[8]);
     }
 
+    // Eq. (eq:recoloringOperator) written for the stored deviations:
+    //   d^r_i = rr rb / rho (phi^b_i - phi^r_i) + rr / rho E_i + term_i
+    //   d^b_i = rr rb / rho (phi^r_i - phi^b_i) + rb / rho E_i - term_i
+    // with E_i the post-collision non-rest part and term_i the recolouring flux.
+    // Each colour is formed from its own density, as in the paper, so a colour
+    // that is absent stays exactly zero (no rounding-level phantom colour).
+    const float fr = rr * inv_rho, fb = rb * inv_rho;
+    const float mix = rr * rb * inv_rho;
     const float F2 = Fx * Fx + Fy * Fy;
     if (F2 > 0.0f) {
         // Eq. (eq:perturbation), one A/2 term per colour: A |F| [W (F.c)^2/|F|^2 - B]
         const float Fn = sqrtf(F2);
         const float invFn = 1.0f / Fn;
-        const float A = d.a_coef * w;
+        const float A = p.a_coef * w;
         const float pa = A * invFn, pb = A * Fn;
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const float Fc = CX(i) * Fx + CY(i) * Fy;
-            n[i] += pa * WT(i) * Fc * Fc - pb * BP(i);
-        }
-        // Eq. (eq:recoloringOperator), cos(phi_i) = c_i.F / (|c_i| |F|)
-        const float fr = rr * inv_rho;
-        const float kk = d.beta * rr * rb * inv_rho * inv_rho * invFn;
-        nr[0] = fr * n[0];
-        nb[0] = n[0] - nr[0];
+        const float kk = p.beta * mix * inv_rho * invFn;   // beta rr rb / rho^2 / |F|
 #pragma unroll
         for (int i = 1; i < 9; i++) {
             const float Fc = CX(i) * Fx + CY(i) * Fy;
+            const float E = e[i] + (pa * WT(i) * Fc * Fc - pb * BP(i));
             const float inv_c = C2(i) == 1 ? 1.0f : 0.70710678118654752f;
-            const float term = kk * Fc * inv_c * (C2(i) == 1 ? rest[1] : rest[2]);
-            nr[i] = fr * n[i] + term;
-            nb[i] = n[i] - nr[i];
+            const float rest = rr * p.phi_r[C2(i)] + rb * p.phi_b[C2(i)];
+            const float term = kk * Fc * inv_c * rest;   // cos(phi_i) = c_i.F / (|c_i| |F|)
+            const float sh = mix * (p.phi_b[C2(i)] - p.phi_r[C2(i)]);
+            dr[i] = sh + fr * E + term;
+            db[i] = -sh + fb * E - term;
         }
     } else {
-        const float fr = rr * inv_rho;
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
-            nr[i] = fr * n[i];
-            nb[i] = n[i] - nr[i];
+        for (int i = 1; i < 9; i++) {
+            const float sh = mix * (p.phi_b[C2(i)] - p.phi_r[C2(i)]);
+            dr[i] = sh + fr * e[i];
+            db[i] = -sh + fb * e[i];
         }
     }
+    dr[0] = 0.0f;
+    db[0] = 0.0f;
 }
 
 // --------------------------------------------------------------- PTX helpers

@@ -24,28 +24,47 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 // ------------------------------------------------------------------ loaders
 
-// Decoded stored value from global memory; ys is wrapped periodically.
+// Stored values from global memory; ys is wrapped periodically.
 template <typename T>
 struct GlobalLoader {
-    const SimDesc *d;
-    int b;
-    __device__ __forceinline__ float operator()(int p, int xs, int ys) const {
-        const int ny = d->ny;
-        const int yw = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-        return Codec<T>::dec(*pop_ptr<T>(*d, b, p, xs, yw), d->ref[p]);
+    const float *rho0;   // &rho[b][0][0][0] (interior column 0)
+    const T *dev0;       // &dev[b][0][0][0]
+    long long rho_plane, dev_plane;
+    int pitch_r, pitch_d, ny;
+    __device__ __forceinline__ GlobalLoader(const SimDesc &d, int b) {
+        rho0 = d.rho + b * d.rho_buf + d.ghost;
+        dev0 = reinterpret_cast<const T *>(d.dev) + b * d.dev_buf + d.ghost;
+        rho_plane = d.rho_plane;
+        dev_plane = d.dev_plane;
+        pitch_r = d.pitch_r;
+        pitch_d = d.pitch_d;
+        ny = d.ph.ny;
+    }
+    __device__ __forceinline__ int wrap(int ys) const { return ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys); }
+    __device__ __forceinline__ float rho(int k, int xs, int ys) const {
+        return rho0[k * rho_plane + (long long)wrap(ys) * pitch_r + xs];
+    }
+    __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
+        return Codec<T>::dec(dev0[(k * 8 + i - 1) * dev_plane + (long long)wrap(ys) * pitch_d + xs]);
     }
 };
 
-// Decoded stored value from the shared-memory row ring; rows y-1, y, y+1.
+// Stored values from the shared-memory row ring (rows y-1, y, y+1 of a strip
+// starting at column x0).  A slot holds [2][BOXW] floats then [16][BOXW] T.
 template <typename T, int BOXW, int G>
 struct SmemLoader {
-    const T *r0, *r1, *r2;
+    const unsigned char *r0, *r1, *r2;
     int y, x0;
-    const float *ref;
-    __device__ __forceinline__ float operator()(int p, int xs, int ys) const {
+    __device__ __forceinline__ const unsigned char *row(int ys) const {
         const int dy = ys - y;
-        const T *r = dy < 0 ? r0 : (dy == 0 ? r1 : r2);
-        return Codec<T>::dec(r[p * BOXW + (xs - x0 + G)], ref[p]);
+        return dy < 0 ? r0 : (dy == 0 ? r1 : r2);
+    }
+    __device__ __forceinline__ float rho(int k, int xs, int ys) const {
+        return reinterpret_cast<const float *>(row(ys))[k * BOXW + (xs - x0 + G)];
+    }
+    __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
+        const T *p = reinterpret_cast<const T *>(row(ys) + 2 * BOXW * sizeof(float));
+        return Codec<T>::dec(p[(k * 8 + i - 1) * BOXW + (xs - x0 + G)]);
     }
 };
 
@@ -53,12 +72,12 @@ struct SmemLoader {
 // to it on the adjacent fluid row (Sec. 2.4 extrapolation).  `psi_of(X)`
 // returns psi of the fluid node in column X of that row.
 template <class PsiOf>
-__device__ __forceinline__ float wall_psi(const SimDesc &d, int X, const PsiOf &psi_of) {
+__device__ __forceinline__ float wall_psi(const Phys &p, int X, const PsiOf &psi_of) {
     float num = 0.0f, den = 0.0f;
 #pragma unroll
     for (int dx = -1; dx <= 1; dx++) {
         const int Xp = X + dx;
-        if (d.bc_x == BC_PERIODIC || (Xp >= 0 && Xp < d.nx)) {
+        if (p.bc_x == BC_PERIODIC || (Xp >= 0 && Xp < p.nx)) {
             const float wgt = dx == 0 ? (1.0f / 9.0f) : (1.0f / 36.0f);
             num += wgt * psi_of(Xp);
             den += wgt;
@@ -82,23 +101,29 @@ __device__ __forceinline__ void s2i4(const V &v, float &gx, float &gy) {
 
 template <typename T, int W, int NSLOT>
 struct FusedCfg {
-    static constexpr int G = 16 / (int)sizeof(T);           // ghost columns each side
+    static constexpr int G = 8;                              // ghost columns each side
     static constexpr int BOXW = W + 2 * G;                   // TMA box width (elements)
-    static constexpr int SLOT_BYTES = ((18 * BOXW * (int)sizeof(T) + 127) / 128) * 128;
-    static constexpr int RING = W + 2;                       // colour-field ring width
+    static constexpr int RHO_BYTES = 2 * BOXW * 4;
+    static constexpr int DEV_BYTES = 16 * BOXW * (int)sizeof(T);
+    static constexpr int SLOT_BYTES = ((RHO_BYTES + DEV_BYTES + 127) / 128) * 128;
+    static constexpr int RING = W + 2;                       // ring width (columns x0-1 .. x0+W)
+    static constexpr int NRING = 5;                          // psi, rho_r, rho_b, q ux, q uy
     static constexpr int DESC_BYTES = ((int)sizeof(SimDesc) + 127) / 128 * 128;
-    static constexpr int RING_BYTES = 3 * 4 * RING * 4;
+    static constexpr int RING_BYTES = NRING * 4 * RING * 4;
     static constexpr int SMEM = DESC_BYTES + NSLOT * SLOT_BYTES + RING_BYTES + NSLOT * 8 + 16;
-    static constexpr uint32_t BOX_BYTES = 18u * BOXW * sizeof(T);
+    static constexpr uint32_t TX_BYTES = (uint32_t)(RHO_BYTES + DEV_BYTES);
     static_assert(BOXW <= 256, "TMA box dimension limit");
-    static_assert((BOXW * sizeof(T)) % 16 == 0, "TMA inner box bytes must be a multiple of 16");
+    static_assert((BOXW * sizeof(T)) % 16 == 0 && (BOXW * 4) % 16 == 0, "TMA inner box bytes");
+    static_assert(RHO_BYTES % 128 == 0, "deviation block of a slot must stay 128-byte aligned");
 };
 
-template <typename T, int W, int NSLOT>
-__global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ descs,
-                                                  const WorkItem *__restrict__ items, int n_items,
-                                                  int step_offset, int *__restrict__ err) {
+template <typename T, int CV, int W, int NSLOT>
+__global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__ descs,
+                                                     const WorkItem *__restrict__ items, int n_items,
+                                                     int step_offset, int *__restrict__ err) {
     using Cfg = FusedCfg<T, W, NSLOT>;
+    constexpr bool HERMITE_SRC = (CV & CV_MRT) && (CV & CV_HERMITE);
+    constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
     constexpr int G = Cfg::G, BOXW = Cfg::BOXW, RING = Cfg::RING;
     extern __shared__ __align__(128) unsigned char smem[];
 
@@ -109,10 +134,12 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
 
     SimDesc &d = *reinterpret_cast<SimDesc *>(smem);
     unsigned char *slots = smem + Cfg::DESC_BYTES;
-    float *psi_s = reinterpret_cast<float *>(slots + NSLOT * Cfg::SLOT_BYTES);
-    float *qux_s = psi_s + 4 * RING;
-    float *quy_s = qux_s + 4 * RING;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(quy_s + 4 * RING);
+    float *ring_psi = reinterpret_cast<float *>(slots + NSLOT * Cfg::SLOT_BYTES);
+    float *ring_rr = ring_psi + 4 * RING;
+    float *ring_rb = ring_rr + 4 * RING;
+    float *ring_qx = ring_rb + 4 * RING;
+    float *ring_qy = ring_qx + 4 * RING;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(ring_qy + 4 * RING);
     volatile int &s_bad = *reinterpret_cast<volatile int *>(bars + NSLOT);
 
     if (smem_u32(slots) & 127) {   // TMA destinations must be 128-byte aligned
@@ -129,17 +156,19 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
         for (int s = 0; s < NSLOT; s++) mbar_init(&bars[s], 1);
         fence_mbar_init();
         fence_proxy_async_smem();
-        tensormap_acquire(&gd->tmap);
+        tensormap_acquire(&gd->tmap_rho);
+        tensormap_acquire(&gd->tmap_dev);
     }
     __syncthreads();
 
+    const Phys p = d.ph;   // per-simulation constants, in registers from here on
     const long long t = d.t0 + step_offset;
     const int bsrc = (int)(t & 1), bdst = bsrc ^ 1;
-    const int nx = d.nx, ny = d.ny;
-    const bool wall_y = d.bc_y == BC_WALL;
-    const bool hermite_src = d.collision == 1 && d.equilibrium == 1;
+    const int nx = p.nx, ny = p.ny;
+    const bool wall_y = p.bc_y == BC_WALL;
     const int x0 = it.x0, w = it.w, ya = it.ya, yb = it.yb;
-    if (w <= 0 || w > W || x0 < 0 || x0 + w > nx || ya < 0 || yb > ny || ya >= yb) {
+    if (d.variant != CV || w <= 0 || w > W || x0 < 0 || x0 + w > nx || (x0 % 8) != 0 || ya < 0 || yb > ny ||
+        ya >= yb) {
         if (tid == 0) atomicOr(err, ERR_BADITEM);
         return;
     }
@@ -148,12 +177,11 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
     auto row_valid = [&](int r) { return !wall_y || (r >= 0 && r < ny); };
     auto slot_of = [&](int r) { return (r - row_first) % NSLOT; };
     auto parity_of = [&](int r) { return (uint32_t)(((r - row_first) / NSLOT) & 1); };
-    auto row_ptr = [&](int r) {
-        return reinterpret_cast<const T *>(slots + slot_of(r) * Cfg::SLOT_BYTES);
-    };
-    // Load source row r into its slot.  A row behind a wall is not loaded, but
-    // its slot barrier still completes one phase (plain arrival) so that the
-    // phase parity of every slot stays (use count) & 1.
+    auto row_ptr = [&](int r) { return slots + slot_of(r) * Cfg::SLOT_BYTES; };
+    // Load source row r (both colour densities and all 16 deviation planes) into
+    // its slot.  A row behind a wall is not loaded, but its slot barrier still
+    // completes one phase (plain arrival) so that every slot's phase parity
+    // stays (use count) & 1.
     auto issue = [&](int r) {
         const int s = slot_of(r);
         if (!row_valid(r)) {
@@ -161,8 +189,11 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
             return;
         }
         const int yr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-        mbar_arrive_expect_tx(&bars[s], Cfg::BOX_BYTES);
-        tma_load_3d(slots + s * Cfg::SLOT_BYTES, &gd->tmap, &bars[s], x0, yr, bsrc * 18);
+        unsigned char *dst = slots + s * Cfg::SLOT_BYTES;
+        mbar_arrive_expect_tx(&bars[s], Cfg::TX_BYTES);
+        // box origin: column x0 - G of the row = element x0 of the padded row
+        tma_load_3d(dst, &gd->tmap_rho, &bars[s], x0, yr, bsrc * 2);
+        tma_load_3d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], x0, yr, bsrc * 16);
     };
     int next_issue = row_first;   // meaningful on thread 0 only
     if (tid == 0) {
@@ -185,11 +216,10 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
         L.r2 = row_ptr(y + 1);
         L.y = y;
         L.x0 = x0;
-        L.ref = d.ref;
         return L;
     };
 
-    // colour field (and q u) of ring row Y for ring columns X = x0 - 1 .. x0 + w
+    // colour field, colour densities (and q u) of ring row Y, columns x0-1 .. x0+w
     auto stageA = [&](int Y) {
         const int rs = ((Y + 4) & 3) * RING;
         if (wall_y && (Y < 0 || Y >= ny)) {
@@ -197,28 +227,30 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
             const auto L = loader(Yn);
             for (int c = tid; c < w + 2; c += W) {
                 const int X = x0 - 1 + c;
-                const float ps = wall_psi(d, X, [&](int Xp) {
-                    float nr[9], nb[9];
-                    pull_node(d, L, Xp, Yn, t, nr, nb);
-                    return node_moments(d, nr, nb).psi;
+                const float ps = wall_psi(p, X, [&](int Xp) {
+                    Pulled P;
+                    pull_node<HERMITE>(p, L, Xp, Yn, t, false, 0.0f, 0.0f, P);
+                    return node_moments(p, P).psi;
                 });
-                psi_s[rs + c] = ps;
-                qux_s[rs + c] = 0.0f;
-                quy_s[rs + c] = 0.0f;
+                ring_psi[rs + c] = ps;
+                ring_qx[rs + c] = 0.0f;
+                ring_qy[rs + c] = 0.0f;
             }
         } else {
             const auto L = loader(Y);
             for (int c = tid; c < w + 2; c += W) {
                 int X = x0 - 1 + c;
-                if (d.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
-                float nr[9], nb[9];
-                pull_node(d, L, X, Y, t, nr, nb);
-                const NodeMoments m = node_moments(d, nr, nb);
-                psi_s[rs + c] = m.psi;
-                if (hermite_src) {
-                    const float q = d.q_r * m.rr + d.q_b * m.rb;
-                    qux_s[rs + c] = q * m.ux;
-                    quy_s[rs + c] = q * m.uy;
+                if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
+                Pulled P;
+                pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                const NodeMoments m = node_moments(p, P);
+                ring_psi[rs + c] = m.psi;
+                ring_rr[rs + c] = m.rr;
+                ring_rb[rs + c] = m.rb;
+                if (HERMITE_SRC) {
+                    const float q = p.q_r * m.rr + p.q_b * m.rb;
+                    ring_qx[rs + c] = q * m.ux;
+                    ring_qy[rs + c] = q * m.uy;
                 }
             }
         }
@@ -227,29 +259,26 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
     auto stageB = [&](int y) {
         if (tid >= w) return;
         const int x = x0 + tid;
-        float nr[9], nb[9];
-        pull_node(d, loader(y), x, y, t, nr, nb);
         const int rm = ((y + 3) & 3) * RING, r0 = ((y + 4) & 3) * RING, rp = ((y + 5) & 3) * RING;
         const int c = tid + 1;
+        Pulled P;
+        pull_node<HERMITE>(p, loader(y), x, y, t, true, ring_rr[r0 + c], ring_rb[r0 + c], P);
         auto ring = [&](const float *f) {
             return [=](int dx, int dy) { return f[(dy < 0 ? rm : (dy == 0 ? r0 : rp)) + c + dx]; };
         };
         float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
-        s2i4(ring(psi_s), Fx, Fy);
-        if (hermite_src) {
+        s2i4(ring(ring_psi), Fx, Fy);
+        if (HERMITE_SRC) {
             float gx_, gy_;
-            s2i4(ring(qux_s), dQx, gy_);
-            s2i4(ring(quy_s), gx_, dQy);
+            s2i4(ring(ring_qx), dQx, gy_);
+            s2i4(ring(ring_qy), gx_, dQy);
         }
-        collide_node(d, nr, nb, Fx, Fy, dQx, dQy);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            store_pop<T>(d, bdst, i, x, y, nr[i]);
-            store_pop<T>(d, bdst, 9 + i, x, y, nb[i]);
-        }
+        float dr[9], db[9];
+        collide_node<CV>(p, P, Fx, Fy, dQx, dQy, dr, db);
+        NodeStore<T>(d, p, bdst, x, y).store(P.rr, P.rb, dr, db);
     };
 
-    // prologue: colour field of rows ya and ya - 1
+    // prologue: ring rows ya and ya - 1
     wait_row(ya - 1);
     wait_row(ya);
     wait_row(ya + 1);
@@ -292,37 +321,44 @@ __global__ void __launch_bounds__(W) k_step_fused(const SimDesc *__restrict__ de
 
 // --------------------------------------------------------- two-pass kernels
 
-// Pass 1: psi and q u of every node into the scratch field aux[3][ny][nx].
-template <typename T>
-__global__ void k_tp_moments(const SimDesc *__restrict__ dp, long long t, float *__restrict__ aux) {
+// Scratch field of the two-pass path: aux[5][ny][nx] = psi, rho_r, rho_b, q u_x, q u_y.
+constexpr int AUX_FIELDS = 5;
+
+// Pass 1: colour field, colour densities and q u of every node.
+template <typename T, int CV>
+__global__ void k_tp_moments(const SimDesc *__restrict__ dp, int step_offset, float *__restrict__ aux) {
+    constexpr bool HERMITE = (CV & CV_HERMITE) != 0, HERMITE_SRC = HERMITE && (CV & CV_MRT);
     const SimDesc &d = *dp;
-    const int nx = d.nx, ny = d.ny;
+    const Phys p = d.ph;
+    const long long t = d.t0 + step_offset;
+    const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
-    const GlobalLoader<T> L{dp, (int)(t & 1)};
-    const bool hermite_src = d.collision == 1 && d.equilibrium == 1;
+    const GlobalLoader<T> L(d, (int)(t & 1));
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx), y = (int)(k / nx);
-        float nr[9], nb[9];
-        pull_node(d, L, x, y, t, nr, nb);
-        const NodeMoments m = node_moments(d, nr, nb);
+        Pulled P;
+        pull_node<HERMITE>(p, L, x, y, t, false, 0.0f, 0.0f, P);
+        const NodeMoments m = node_moments(p, P);
         aux[k] = m.psi;
-        if (hermite_src) {
-            const float q = d.q_r * m.rr + d.q_b * m.rb;
-            aux[n + k] = q * m.ux;
-            aux[2 * n + k] = q * m.uy;
+        aux[n + k] = m.rr;
+        aux[2 * n + k] = m.rb;
+        if (HERMITE_SRC) {
+            const float q = p.q_r * m.rr + p.q_b * m.rb;
+            aux[3 * n + k] = q * m.ux;
+            aux[4 * n + k] = q * m.uy;
         }
     }
 }
 
 // Value of an aux field at lattice position (X, Y) next to the domain.
-__device__ __forceinline__ float aux_at(const SimDesc &d, const float *f, int X, int Y, bool is_psi) {
-    const int nx = d.nx, ny = d.ny;
+__device__ __forceinline__ float aux_at(const Phys &p, const float *f, int X, int Y, bool is_psi) {
+    const int nx = p.nx, ny = p.ny;
     if (Y < 0 || Y >= ny) {
-        if (d.bc_y == BC_WALL) {
+        if (p.bc_y == BC_WALL) {
             if (!is_psi) return 0.0f;
             const int Yn = Y < 0 ? 0 : ny - 1;
-            return wall_psi(d, X, [&](int Xp) {
+            return wall_psi(p, X, [&](int Xp) {
                 const int xw = Xp < 0 ? Xp + nx : (Xp >= nx ? Xp - nx : Xp);
                 return f[(long long)Yn * nx + xw];
             });
@@ -330,7 +366,7 @@ __device__ __forceinline__ float aux_at(const SimDesc &d, const float *f, int X,
         Y = Y < 0 ? Y + ny : Y - ny;
     }
     if (X < 0 || X >= nx) {
-        if (d.bc_x == BC_PERIODIC) X = X < 0 ? X + nx : X - nx;
+        if (p.bc_x == BC_PERIODIC) X = X < 0 ? X + nx : X - nx;
         else X = X < 0 ? 0 : nx - 1;
     }
     return f[(long long)Y * nx + X];
@@ -338,101 +374,146 @@ __device__ __forceinline__ float aux_at(const SimDesc &d, const float *f, int X,
 
 // Pass 2: gradient from the scratch field, collision, perturbation,
 // recolouring and store of every node.
-template <typename T>
-__global__ void k_tp_collide(const SimDesc *__restrict__ dp, long long t, const float *__restrict__ aux) {
+template <typename T, int CV>
+__global__ void k_tp_collide(const SimDesc *__restrict__ dp, int step_offset, const float *__restrict__ aux) {
+    constexpr bool HERMITE = (CV & CV_HERMITE) != 0, HERMITE_SRC = HERMITE && (CV & CV_MRT);
     const SimDesc &d = *dp;
-    const int nx = d.nx, ny = d.ny;
+    const Phys p = d.ph;
+    const long long t = d.t0 + step_offset;
+    const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
     const int bsrc = (int)(t & 1);
-    const GlobalLoader<T> L{dp, bsrc};
-    const bool hermite_src = d.collision == 1 && d.equilibrium == 1;
+    const GlobalLoader<T> L(d, bsrc);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx), y = (int)(k / nx);
-        float nr[9], nb[9];
-        pull_node(d, L, x, y, t, nr, nb);
+        Pulled P;
+        pull_node<HERMITE>(p, L, x, y, t, true, aux[n + k], aux[2 * n + k], P);
         float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
-        s2i4([&](int dx, int dy) { return aux_at(d, aux, x + dx, y + dy, true); }, Fx, Fy);
-        if (hermite_src) {
+        s2i4([&](int dx, int dy) { return aux_at(p, aux, x + dx, y + dy, true); }, Fx, Fy);
+        if (HERMITE_SRC) {
             float gx_, gy_;
-            s2i4([&](int dx, int dy) { return aux_at(d, aux + n, x + dx, y + dy, false); }, dQx, gy_);
-            s2i4([&](int dx, int dy) { return aux_at(d, aux + 2 * n, x + dx, y + dy, false); }, gx_, dQy);
+            s2i4([&](int dx, int dy) { return aux_at(p, aux + 3 * n, x + dx, y + dy, false); }, dQx, gy_);
+            s2i4([&](int dx, int dy) { return aux_at(p, aux + 4 * n, x + dx, y + dy, false); }, gx_, dQy);
         }
-        collide_node(d, nr, nb, Fx, Fy, dQx, dQy);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            store_pop<T>(d, bsrc ^ 1, i, x, y, nr[i]);
-            store_pop<T>(d, bsrc ^ 1, 9 + i, x, y, nb[i]);
-        }
+        float dr[9], db[9];
+        collide_node<CV>(p, P, Fx, Fy, dQx, dQy, dr, db);
+        NodeStore<T>(d, p, bsrc ^ 1, x, y).store(P.rr, P.rb, dr, db);
     }
 }
 
 // ------------------------------------------------------------ init / fields
 
-// Equilibrium state from FP64 fields, written into the slots the first pull
-// reads so that pulling at t = 0 yields N^k_i(x, 0) = N^{k(e)}_i (buffer 0).
+// Equilibrium state from FP64 fields at t = 0.  The stored state is the one
+// whose first pull yields N^k_i(x, 0) = N^{k(e)}_i(x): the slot (i, y) holds
+// the equilibrium population of the node that will read it -- node y + c_i,
+// or node y itself in direction opp(i) when that link is bounced by a wall.
+// The stored colour density of y is the sum of its slots, the deviations are
+// taken from it.
+// With `pops` non-null the pre-collision populations N^k_i(x, 0) are given
+// directly (layout [2][9][ny][nx]) instead of being the equilibria of the fields.
 template <typename T>
 __global__ void k_init(const SimDesc *__restrict__ dp, const double *__restrict__ rr,
                        const double *__restrict__ rb, const double *__restrict__ ux,
-                       const double *__restrict__ uy) {
+                       const double *__restrict__ uy, const double *__restrict__ pops) {
     const SimDesc &d = *dp;
-    const int nx = d.nx, ny = d.ny;
+    const Phys p = d.ph;
+    const bool hermite = (d.variant & CV_HERMITE) != 0;
+    const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
+    const double herm[2] = {p.herm_r, p.herm_b};
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx), y = (int)(k / nx);
-        const double vx = ux[k], vy = uy[k], usq = vx * vx + vy * vy;
-        const double rho[2] = {rr[k], rb[k]};
-        const double herm[2] = {d.herm_r, d.herm_b};
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
+        // equilibrium population i of colour kk at node (X, Y) (in the domain)
+        auto feq = [&](int kk, int i, int X, int Y) {
+            const long long m = (long long)Y * nx + X;
+            if (pops) return pops[(long long)(kk * 9 + i) * n + m];
+            const double vx = ux[m], vy = uy[m], usq = vx * vx + vy * vy;
+            const double rho = kk == 0 ? rr[m] : rb[m];
             const double cu = CX(i) * vx + CY(i) * vy;
             double lin = 3.0 * cu;
-            int xs = x - CX(i), ys = y - CY(i), plane = i, xd = x, yd = y;
+            if (hermite) lin = 3.0 * cu * (1.0 + 0.5 * herm[kk] * (3.0 * C2(i) - 4.0));
+            return rho * (double)phi_k(p, kk, C2(i)) + rho * WT(i) * (lin + 4.5 * cu * cu - 1.5 * usq);
+        };
+        double v[2][9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            int X = x + CX(i), Y = y + CY(i);
+            int mode = 0;   // 0: read by node (X, Y), 1: bounced back to (x, y), 2: unread
+            if (i != 0) {
+                if (Y < 0 || Y >= ny) {
+                    if (p.bc_y == BC_WALL) mode = 1;
+                    else Y = Y < 0 ? Y + ny : Y - ny;
+                }
+                if (mode == 0 && (X < 0 || X >= nx)) {
+                    if (p.bc_x == BC_PERIODIC) X = X < 0 ? X + nx : X - nx;
+                    else mode = 2;
+                }
+            }
             for (int kk = 0; kk < 2; kk++) {
-                const double phi = kk == 0 ? d.phi_r[C2(i)] : d.phi_b[C2(i)];
-                double l = lin;
-                if (d.equilibrium) l = 3.0 * cu * (1.0 + 0.5 * herm[kk] * (3.0 * C2(i) - 4.0));
-                const double feq = rho[kk] * phi + rho[kk] * WT(i) * (l + 4.5 * cu * cu - 1.5 * usq);
-                if (ys < 0 || ys >= ny) {
-                    if (d.bc_y == BC_WALL) {
-                        store_pop<T>(d, 0, kk * 9 + OPP(i), x, y, (float)feq);
-                        continue;
-                    }
-                    yd = ys < 0 ? ys + ny : ys - ny;
-                } else {
-                    yd = ys;
-                }
-                if (xs < 0 || xs >= nx) {
-                    if (d.bc_x != BC_PERIODIC) continue;   // unknown at an open boundary
-                    xd = xs < 0 ? xs + nx : xs - nx;
-                } else {
-                    xd = xs;
-                }
-                store_pop<T>(d, 0, kk * 9 + plane, xd, yd, (float)feq);
+                if (mode == 0) v[kk][i] = feq(kk, i, X, Y);
+                else if (mode == 1) v[kk][i] = feq(kk, OPP(i), x, y);
+                else v[kk][i] = pops ? pops[(long long)(kk * 9 + i) * n + k]
+                                     : (double)phi_k(p, kk, C2(i)) * (kk == 0 ? rr[k] : rb[k]);
             }
         }
+        float dr[9], db[9];
+        double rs[2];
+        for (int kk = 0; kk < 2; kk++) {
+            double s = 0.0;
+            for (int i = 0; i < 9; i++) s += v[kk][i];
+            rs[kk] = s;
+            for (int i = 1; i < 9; i++) {
+                const float dv = (float)(v[kk][i] - (double)phi_k(p, kk, C2(i)) * s);
+                if (kk == 0) dr[i] = dv; else db[i] = dv;
+            }
+        }
+        dr[0] = db[0] = 0.0f;
+        NodeStore<T>(d, p, 0, x, y).store((float)rs[0], (float)rs[1], dr, db);
     }
 }
 
 // Macroscopic fields of the state at time t (pre-collision moments).
-template <typename T>
+template <typename T, bool HERMITE>
 __global__ void k_fields(const SimDesc *__restrict__ dp, long long t, double *__restrict__ out) {
     const SimDesc &d = *dp;
-    const int nx = d.nx, ny = d.ny;
+    const Phys p = d.ph;
+    const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
-    const GlobalLoader<T> L{dp, (int)(t & 1)};
+    const GlobalLoader<T> L(d, (int)(t & 1));
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx), y = (int)(k / nx);
-        float nr[9], nb[9];
-        pull_node(d, L, x, y, t, nr, nb);
-        const NodeMoments m = node_moments(d, nr, nb);
+        Pulled P;
+        pull_node<HERMITE>(p, L, x, y, t, false, 0.0f, 0.0f, P);
+        const NodeMoments m = node_moments(p, P);
         out[k] = m.rr;
         out[n + k] = m.rb;
         out[2 * n + k] = m.ux;
         out[3 * n + k] = m.uy;
-        out[4 * n + k] = (double)m.rr * d.cs2_r + (double)m.rb * d.cs2_b;
+        out[4 * n + k] = (double)m.rr * p.cs2_r + (double)m.rb * p.cs2_b;
+    }
+}
+
+// Pre-collision populations of every node at time t, layout [2][9][ny][nx].
+template <typename T, bool HERMITE>
+__global__ void k_read_pops(const SimDesc *__restrict__ dp, long long t, double *__restrict__ out) {
+    const SimDesc &d = *dp;
+    const Phys p = d.ph;
+    const int nx = p.nx, ny = p.ny;
+    const long long n = (long long)nx * ny;
+    const GlobalLoader<T> L(d, (int)(t & 1));
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        double nr[9], nb[9];
+        pull_populations<HERMITE>(p, L, x, y, t, nr, nb);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            out[i * n + k] = nr[i];
+            out[(9 + i) * n + k] = nb[i];
+        }
     }
 }
 
@@ -472,23 +553,24 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[DIAG_NQ], doubl
 // pass 0: mass_r, mass_b, mom_x, mom_y, area_b, max|u| (slot 5), sum x w_b, sum y w_b,
 //         sum ux w_b, sum ux w_r, sum w_r, nonfinite
 // pass 1: sum p (r < r_in), count, sum p (r > r_out), count around (cx, cy)
-template <typename T>
+template <typename T, bool HERMITE>
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag(const SimDesc *__restrict__ dp, long long t, int pass,
                                                        double cx, double cy, double r_in, double r_out,
                                                        double *__restrict__ part) {
     const SimDesc &d = *dp;
-    const int nx = d.nx, ny = d.ny;
+    const Phys p = d.ph;
+    const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
-    const GlobalLoader<T> L{dp, (int)(t & 1)};
+    const GlobalLoader<T> L(d, (int)(t & 1));
     double acc[DIAG_NQ];
 #pragma unroll
     for (int q = 0; q < DIAG_NQ; q++) acc[q] = 0.0;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx), y = (int)(k / nx);
-        float nr[9], nb[9];
-        pull_node(d, L, x, y, t, nr, nb);
-        const NodeMoments m = node_moments(d, nr, nb);
+        Pulled P;
+        pull_node<HERMITE>(p, L, x, y, t, false, 0.0f, 0.0f, P);
+        const NodeMoments m = node_moments(p, P);
         const double rho = (double)m.rr + m.rb;
         if (pass == 0) {
             const bool bad = !(isfinite(m.rr) && isfinite(m.rb) && isfinite(m.ux) && isfinite(m.uy));
@@ -507,12 +589,12 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag(const SimDesc *__restrict
             acc[10] += wr;
         } else {
             double dx = fabs(x - cx), dy = fabs(y - cy);
-            if (d.bc_x == BC_PERIODIC) dx = fmin(dx, nx - dx);
-            if (d.bc_y == BC_PERIODIC) dy = fmin(dy, ny - dy);
+            if (p.bc_x == BC_PERIODIC) dx = fmin(dx, nx - dx);
+            if (p.bc_y == BC_PERIODIC) dy = fmin(dy, ny - dy);
             const double r = sqrt(dx * dx + dy * dy);
-            const double p = (double)m.rr * d.cs2_r + (double)m.rb * d.cs2_b;
-            if (r < r_in) { acc[0] += p; acc[1] += 1.0; }
-            if (r > r_out) { acc[2] += p; acc[3] += 1.0; }
+            const double pr = (double)m.rr * p.cs2_r + (double)m.rb * p.cs2_b;
+            if (r < r_in) { acc[0] += pr; acc[1] += 1.0; }
+            if (r > r_out) { acc[2] += pr; acc[3] += 1.0; }
         }
     }
     block_reduce_store(acc, part);

@@ -34,7 +34,7 @@ _STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4:
 # The C functions every build exports (declared in include/lbm.h).
 ABI_SYMBOLS = (
     "lbm_default_params", "lbm_bytes_required", "lbm_create", "lbm_create_ex", "lbm_init_bubble",
-    "lbm_init_slug", "lbm_init_fields", "lbm_step", "lbm_synchronize", "lbm_time", "lbm_read_fields",
+    "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
     "lbm_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_last_error",
     "lbm_destroy", "lbm_batch_create", "lbm_batch_step", "lbm_batch_items", "lbm_batch_destroy",
 )
@@ -106,11 +106,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbm_init_bubble.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     L.lbm_init_slug.argtypes = [vp, i, ctypes.c_double, ctypes.c_double, i]
     L.lbm_init_fields.argtypes = [vp, dp, dp, dp, dp]
+    L.lbm_init_populations.argtypes = [vp, dp]
     L.lbm_step.argtypes = [vp, l]
     L.lbm_synchronize.argtypes = [vp]
     L.lbm_time.argtypes = [vp]
     L.lbm_time.restype = ctypes.c_longlong
     L.lbm_read_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+    L.lbm_read_populations.argtypes = [vp, dp]
     L.lbm_diagnostics.argtypes = [vp, ctypes.POINTER(lbm_diag)]
     L.lbm_state_bytes.argtypes = [vp]
     L.lbm_state_bytes.restype = st
@@ -178,6 +180,11 @@ def lbm_init_fields(sim: int, rho_r, rho_b, ux, uy):
     _check(load().lbm_init_fields(sim, *[_dptr(v) for v in a]), sim)
 
 
+def lbm_init_populations(sim: int, pops):
+    a = np.ascontiguousarray(pops, dtype=np.float64)
+    _check(load().lbm_init_populations(sim, _dptr(a)), sim)
+
+
 def lbm_step(sim: int, n: int):
     _check(load().lbm_step(sim, int(n)), sim)
 
@@ -193,6 +200,12 @@ def lbm_time(sim: int) -> int:
 def lbm_read_fields(sim: int, nx: int, ny: int) -> dict:
     out = {k: np.empty((ny, nx)) for k in ("rho_r", "rho_b", "ux", "uy", "p")}
     _check(load().lbm_read_fields(sim, *[_dptr(out[k]) for k in ("rho_r", "rho_b", "ux", "uy", "p")]), sim)
+    return out
+
+
+def lbm_read_populations(sim: int, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((2, 9, ny, nx))
+    _check(load().lbm_read_populations(sim, _dptr(out)), sim)
     return out
 
 
@@ -314,6 +327,10 @@ class Simulation:
     def init_fields(self, rho_r, rho_b, ux, uy):
         lbm_init_fields(self.h, rho_r, rho_b, ux, uy)
 
+    def init_populations(self, pops):
+        """pops: array (2, 9, ny, nx) of pre-collision populations."""
+        lbm_init_populations(self.h, pops)
+
     def step(self, n: int = 1):
         lbm_step(self.h, n)
 
@@ -322,6 +339,10 @@ class Simulation:
 
     def fields(self) -> dict:
         return lbm_read_fields(self.h, self.nx, self.ny)
+
+    def populations(self) -> np.ndarray:
+        """Pre-collision populations, array (2, 9, ny, nx)."""
+        return lbm_read_populations(self.h, self.nx, self.ny)
 
     def diagnostics(self, allow_unstable: bool = False) -> dict:
         return lbm_diagnostics(self.h, allow_unstable)

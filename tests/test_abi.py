@@ -41,10 +41,11 @@ def test_library_exports_every_declared_symbol(lib):
 def test_host_only_calls():
     p = L.lbm_default_params()
     assert p.alpha_b == 0.2 and p.delta == 0.1 and p.beta == 0.99 and abs(p.mrt_lambda - 0.8) < 1e-15
-    # 2 buffers x 18 planes x ny x pitch x 4 bytes, pitch = nx + 8 rounded to 4
-    assert L.lbm_bytes_required(64, 32, p) == 2 * 18 * 32 * 72 * 4
+    # 2 buffers x (2 FP32 density planes + 16 deviation planes) x ny x pitch,
+    # pitch = nx + 2 * 8 ghost columns rounded to 16 bytes
+    assert L.lbm_bytes_required(64, 32, p) == 2 * 2 * 32 * 80 * 4 + 2 * 16 * 32 * 80 * 4
     p.storage = L.LBM_F16DEV
-    assert L.lbm_bytes_required(64, 32, p) == 2 * 18 * 32 * 80 * 2
+    assert L.lbm_bytes_required(64, 32, p) == 2 * 2 * 32 * 80 * 4 + 2 * 16 * 32 * 80 * 2
     bad = L.lbm_default_params()
     bad.tau_r = 0.5
     assert L.lbm_bytes_required(64, 32, bad) == 0
