@@ -82,7 +82,8 @@ struct lbm_sim {
     long long t = 0;
     long long dev_t0 = -1;       // t0 last written into d_desc
     WorkItem *d_items = nullptr;
-    int n_items = 0;
+    int *d_off = nullptr;        // per-block item ranges of the plan
+    int n_items = 0, n_blocks = 0;
     int *d_err = nullptr;
     float *d_aux = nullptr;      // two-pass scratch field
     double *d_part = nullptr;    // diagnostic partials + final
@@ -99,9 +100,11 @@ struct lbm_batch {
     std::vector<long long> t_mirror;  // t0 of each batch descriptor as last written
     SimDesc *d_descs = nullptr;
     WorkItem *d_items = nullptr;
+    int *d_off = nullptr;
     int n_items = 0;
-    // one launch per (storage, variant) group; items of a group are contiguous
-    struct Group { int storage, variant, first, count; };
+    // one launch per (storage, variant) group: items [item0, ...) and block
+    // ranges off[off0 .. off0 + blocks]
+    struct Group { int storage, variant, item0, off0, blocks; };
     std::vector<Group> groups;
     int *d_err = nullptr;
     cudaStream_t stream = nullptr;
@@ -264,33 +267,94 @@ lbm_status encode_tmap(lbm_sim *s) {
     return LBM_OK;
 }
 
-// Rows each block marches over for a lattice of `strip_rows` strip-rows in total.
-int default_rows_per_item(long long strip_rows, int ny) {
-    const long long target = 152LL * 3 * 2;                 // ~two waves of resident blocks
-    long long L = (strip_rows + target - 1) / target;
-    L = std::max<long long>(L, 8);
-    L = std::min<long long>(L, 64);
-    return (int)std::min<long long>(L, ny);
+// ---- work plans: which block marches over which rows of which strip
+
+struct StripRef {
+    int sim, x0, w, ny;
+};
+
+struct Plan {
+    std::vector<WorkItem> items;
+    std::vector<int> off;   // block b owns items [off[b], off[b+1])
+    int blocks = 0;
+};
+
+void strips_of(std::vector<StripRef> &out, int sim, int nx, int ny) {
+    for (int x0 = 0; x0 < nx; x0 += FUSED_W) out.push_back({sim, x0, std::min(FUSED_W, nx - x0), ny});
 }
 
-void build_items(std::vector<WorkItem> &out, int sim, int nx, int ny, int L) {
-    for (int x0 = 0; x0 < nx; x0 += FUSED_W) {
-        const int w = std::min(FUSED_W, nx - x0);
-        for (int ya = 0; ya < ny; ya += L) {
+constexpr int MIN_PIECE = 8;   // shortest row range worth a 4-row halo
+
+// Balanced persistent plan: the strip rows (weighted by the warps a strip
+// keeps busy) are cut into max_blocks nearly equal shares, in order, so a block
+// may march over the end of one strip and the start of the next.
+Plan balanced_plan(const std::vector<StripRef> &strips, int max_blocks) {
+    Plan P;
+    double total = 0.0;
+    for (const auto &s : strips) total += (double)s.ny * ((s.w + 31) / 32);
+    const double full_rows = total / 4.0;
+    int B = (int)std::min<double>(max_blocks, std::max(1.0, std::floor(full_rows / MIN_PIECE)));
+    const double quota = total / B;
+    P.off.push_back(0);
+    int b = 0;
+    double acc = 0.0;
+    for (const auto &s : strips) {
+        const int wc = (s.w + 31) / 32;
+        int y = 0;
+        while (y < s.ny) {
+            const double left = quota * (b + 1) - acc;
+            int take = (int)std::floor(left / wc + 1e-9);
+            if (take < MIN_PIECE && b < B - 1 && (int)P.items.size() > P.off.back()) {
+                P.off.push_back((int)P.items.size());   // close block b, continue in b + 1
+                ++b;
+                continue;
+            }
+            take = std::max(take, MIN_PIECE);
+            take = std::min(take, s.ny - y);
+            if (s.ny - (y + take) < MIN_PIECE) take = s.ny - y;   // no tiny tail pieces
             WorkItem it{};
-            it.sim = sim;
-            it.x0 = x0;
-            it.w = w;
-            it.ya = ya;
-            it.yb = std::min(ny, ya + L);
-            out.push_back(it);
+            it.sim = s.sim;
+            it.x0 = s.x0;
+            it.w = s.w;
+            it.ya = y;
+            it.yb = y + take;
+            P.items.push_back(it);
+            acc += (double)take * wc;
+            y += take;
+            if (acc >= quota * (b + 1) - 1e-9 && b < B - 1) {
+                P.off.push_back((int)P.items.size());
+                ++b;
+            }
         }
     }
+    while ((int)P.off.size() < B + 1) P.off.push_back((int)P.items.size());
+    P.off.back() = (int)P.items.size();
+    P.blocks = B;
+    return P;
+}
+
+// Fixed plan: every strip cut into pieces of `rows` rows, one piece per block.
+Plan fixed_plan(const std::vector<StripRef> &strips, int rows) {
+    Plan P;
+    P.off.push_back(0);
+    for (const auto &s : strips)
+        for (int y = 0; y < s.ny; y += rows) {
+            WorkItem it{};
+            it.sim = s.sim;
+            it.x0 = s.x0;
+            it.w = s.w;
+            it.ya = y;
+            it.yb = std::min(s.ny, y + rows);
+            P.items.push_back(it);
+            P.off.push_back((int)P.items.size());
+        }
+    P.blocks = (int)P.items.size();
+    return P;
 }
 
 template <typename T, int CV>
-cudaError_t launch_fused_t(const SimDesc *descs, const WorkItem *items, int n_items, int off, int *err,
-                           cudaStream_t st) {
+cudaError_t launch_fused_t(const SimDesc *descs, const WorkItem *items, const int *item_off, int n_blocks, int off,
+                           int *err, cudaStream_t st) {
     static bool attr_done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -300,29 +364,47 @@ cudaError_t launch_fused_t(const SimDesc *descs, const WorkItem *items, int n_it
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
-    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_items, FUSED_W, fused_smem<T>(), st>>>(descs, items, n_items, off,
-                                                                                      err);
+    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_blocks, FUSED_W, fused_smem<T>(), st>>>(descs, items, item_off,
+                                                                                       n_blocks, off, err);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fused_v(int variant, const SimDesc *descs, const WorkItem *items, int n_items, int off, int *err,
-                           cudaStream_t st) {
+cudaError_t launch_fused_v(int variant, const SimDesc *descs, const WorkItem *items, const int *item_off,
+                           int n_blocks, int off, int *err, cudaStream_t st) {
     switch (variant) {
-    case 0: return launch_fused_t<T, 0>(descs, items, n_items, off, err, st);
-    case CV_MRT: return launch_fused_t<T, CV_MRT>(descs, items, n_items, off, err, st);
-    case CV_HERMITE: return launch_fused_t<T, CV_HERMITE>(descs, items, n_items, off, err, st);
-    default: return launch_fused_t<T, CV_MRT | CV_HERMITE>(descs, items, n_items, off, err, st);
+    case 0: return launch_fused_t<T, 0>(descs, items, item_off, n_blocks, off, err, st);
+    case CV_MRT: return launch_fused_t<T, CV_MRT>(descs, items, item_off, n_blocks, off, err, st);
+    case CV_HERMITE: return launch_fused_t<T, CV_HERMITE>(descs, items, item_off, n_blocks, off, err, st);
+    default: return launch_fused_t<T, CV_MRT | CV_HERMITE>(descs, items, item_off, n_blocks, off, err, st);
     }
 }
 
-cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, const WorkItem *items, int n_items,
-                             int off, int *err, cudaStream_t st) {
+cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, const WorkItem *items,
+                             const int *item_off, int n_blocks, int off, int *err, cudaStream_t st) {
     switch (storage) {
-    case ST_F32: return launch_fused_v<float>(variant, descs, items, n_items, off, err, st);
-    case ST_F16DEV: return launch_fused_v<__half>(variant, descs, items, n_items, off, err, st);
-    default: return launch_fused_v<__nv_bfloat16>(variant, descs, items, n_items, off, err, st);
+    case ST_F32: return launch_fused_v<float>(variant, descs, items, item_off, n_blocks, off, err, st);
+    case ST_F16DEV: return launch_fused_v<__half>(variant, descs, items, item_off, n_blocks, off, err, st);
+    default: return launch_fused_v<__nv_bfloat16>(variant, descs, items, item_off, n_blocks, off, err, st);
     }
+}
+
+// Resident fused blocks per SM for a storage type (occupancy query), times SMs.
+int resident_blocks(int storage) {
+    static int cache[3] = {0, 0, 0};
+    if (cache[storage]) return cache[storage];
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void *k = storage == ST_F32 ? fused_kernel_ptr<float, 0>()
+                    : storage == ST_F16DEV ? fused_kernel_ptr<__half, 0>() : fused_kernel_ptr<__nv_bfloat16, 0>();
+    const int smem = storage == ST_F32 ? fused_smem<float>() : storage == ST_F16DEV ? fused_smem<__half>()
+                                                                                     : fused_smem<__nv_bfloat16>();
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, FUSED_W, smem) != cudaSuccess || per < 1) per = 1;
+    if (sms < 1) sms = 1;
+    cache[storage] = sms * per;
+    return cache[storage];
 }
 
 int grid_for(long long n, int threads) {
@@ -435,8 +517,8 @@ lbm_status check_err_word(lbm_sim *s, int *d_err) {
 lbm_status step_direct(lbm_sim *s, long n) {
     for (long j = 0; j < n; j++) {
         if (use_fused(s)) {
-            CK(launch_fused_any(s->p.storage, s->h.variant, s->d_desc, s->d_items, s->n_items, (int)j, s->d_err,
-                                s->stream));
+            CK(launch_fused_any(s->p.storage, s->h.variant, s->d_desc, s->d_items, s->d_off, s->n_blocks, (int)j,
+                                s->d_err, s->stream));
         } else {
             CK(launch_twopass(s, (int)j));
         }
@@ -531,13 +613,20 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         set_err(s->err, "cudaMalloc of descriptor failed");
         return fail(LBM_ENOMEM);
     }
-    std::vector<WorkItem> items;
-    const long long strips = (nx + FUSED_W - 1) / FUSED_W;
-    build_items(items, 0, nx, ny, default_rows_per_item(strips * ny, ny));
-    s->n_items = (int)items.size();
-    if (cudaMalloc(&s->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess) {
-        set_err(s->err, "cudaMalloc of work items failed");
-        return fail(LBM_ENOMEM);
+    {
+        std::vector<StripRef> strips;
+        strips_of(strips, 0, nx, ny);
+        Plan P = balanced_plan(strips, resident_blocks(p->storage));
+        s->n_items = (int)P.items.size();
+        s->n_blocks = P.blocks;
+        if (cudaMalloc(&s->d_items, P.items.size() * sizeof(WorkItem)) != cudaSuccess ||
+            cudaMalloc(&s->d_off, P.off.size() * sizeof(int)) != cudaSuccess ||
+            cudaMemcpy(s->d_items, P.items.data(), P.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(s->d_off, P.off.data(), P.off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_err(s->err, "work plan upload failed");
+            return fail(LBM_ENOMEM);
+        }
     }
     const size_t nn = (size_t)nx * ny;
     if (p->kernel == LBM_KERNEL_TWOPASS && cudaMalloc(&s->d_aux, AUX_FIELDS * nn * sizeof(float)) != cudaSuccess) {
@@ -550,8 +639,6 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         return fail(LBM_ENOMEM);
     }
     if (cudaMemcpyAsync(s->d_desc, &s->h, sizeof(SimDesc), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-        cudaMemcpyAsync(s->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
-                        s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream) != cudaSuccess ||
         cudaMemsetAsync(s->pop, 0, s->pop_bytes, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess) {
@@ -813,6 +900,7 @@ void lbm_destroy(lbm_sim *s) {
     if (s->own_pop && s->pop) cudaFree(s->pop);
     cudaFree(s->d_desc);
     cudaFree(s->d_items);
+    cudaFree(s->d_off);
     cudaFree(s->d_err);
     cudaFree(s->d_aux);
     cudaFree(s->d_part);
@@ -844,22 +932,28 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
         b->t_mirror.push_back(sims[i]->t);
     }
     // items grouped by (storage, variant): one launch per group and step
+    std::vector<int> offs;
     for (int st = 0; st < 3; st++)
         for (int cv = 0; cv < 4; cv++) {
-            const int first = (int)items.size();
-            for (int i = 0; i < n; i++) {
-                if (sims[i]->p.storage != st || sims[i]->h.variant != cv) continue;
-                const int L = rows_per_item > 0 ? rows_per_item : default_rows_per_item(strip_rows, sims[i]->ny);
-                build_items(items, i, sims[i]->nx, sims[i]->ny, std::min(L, sims[i]->ny));
-            }
-            if ((int)items.size() > first) b->groups.push_back({st, cv, first, (int)items.size() - first});
+            std::vector<StripRef> strips;
+            for (int i = 0; i < n; i++)
+                if (sims[i]->p.storage == st && sims[i]->h.variant == cv) strips_of(strips, i, sims[i]->nx, sims[i]->ny);
+            if (strips.empty()) continue;
+            Plan P = rows_per_item > 0 ? fixed_plan(strips, rows_per_item) : balanced_plan(strips, resident_blocks(st));
+            lbm_batch::Group g{st, cv, (int)items.size(), (int)offs.size(), P.blocks};
+            for (int &o : P.off) o += g.item0;
+            items.insert(items.end(), P.items.begin(), P.items.end());
+            offs.insert(offs.end(), P.off.begin(), P.off.end());
+            b->groups.push_back(g);
         }
     b->n_items = (int)items.size();
     if (cudaMalloc(&b->d_descs, n * sizeof(SimDesc)) != cudaSuccess ||
         cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess ||
+        cudaMalloc(&b->d_off, offs.size() * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_err, sizeof(int)) != cudaSuccess ||
         cudaMemcpy(b->d_descs, descs.data(), n * sizeof(SimDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_off, offs.data(), offs.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
         set_err(g_create_err, "batch allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
         lbm_batch_destroy(b);
@@ -890,8 +984,8 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
     auto run = [&](long k) -> lbm_status {
         for (long j = 0; j < k; j++)
             for (const auto &g : b->groups)
-                CK(launch_fused_any(g.storage, g.variant, b->d_descs, b->d_items + g.first, g.count, (int)j, b->d_err,
-                                    b->stream));
+                CK(launch_fused_any(g.storage, g.variant, b->d_descs, b->d_items, b->d_off + g.off0, g.blocks, (int)j,
+                                    b->d_err, b->stream));
         k_advance<<<(nsims + 127) / 128, 128, 0, b->stream>>>(b->d_descs, nsims, k);
         CK(cudaGetLastError());
         return LBM_OK;
@@ -935,6 +1029,7 @@ void lbm_batch_destroy(lbm_batch *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaFree(b->d_descs);
     cudaFree(b->d_items);
+    cudaFree(b->d_off);
     cudaFree(b->d_err);
     delete b;
 }

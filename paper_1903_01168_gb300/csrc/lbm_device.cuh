@@ -303,6 +303,61 @@ __device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x
         P.e[i] = (float)((nr[i] + nb[i]) - (rrf * (double)p.phi_r[C2(i)] + rbf * (double)p.phi_b[C2(i)]));
 }
 
+// Moments of the pulled node (x, y) without forming its populations: the new
+// colour densities
+//   rho_k' = rho_k(x) + sum_{i>=1} [phi^k_i (s^k_i - rho_k(x)) + delta^k_i - d^k_i(x)]
+// (s, delta: density and deviation of the source of direction i) and, with
+// NEED_J, the momentum sum_i c_i N_i summed over opposite pairs.  Open columns
+// take the full pull.
+template <bool HERMITE, bool NEED_J, class Loader>
+__device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                             float &rr, float &rb, float &jx, float &jy) {
+    if (p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1)) {
+        Pulled P;
+        pull_node<HERMITE>(p, ld, x, y, t, false, 0.0f, 0.0f, P);
+        rr = P.rr;
+        rb = P.rb;
+        jx = (P.e[1] - P.e[3]) + (P.e[5] - P.e[7]) + (P.e[8] - P.e[6]);
+        jy = (P.e[2] - P.e[4]) + (P.e[5] - P.e[7]) + (P.e[6] - P.e[8]);
+        return;
+    }
+    const bool wall_y = p.bc_y == BC_WALL;
+    const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
+    float n[2][9];   // n[k][i] = N^k_i - phi^k_i rho_k(x) for i >= 1 (small)
+    float acc[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const float own = ld.rho(k, x, y);
+        float a = 0.0f;
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+            float sv, dv;
+            if (bounce) {
+                sv = own;
+                dv = ld.dev(k, OPP(i), x, y);
+            } else {
+                sv = ld.rho(k, x - CX(i), y - CY(i));
+                dv = ld.dev(k, i, x - CX(i), y - CY(i));
+            }
+            n[k][i] = phi_k(p, k, C2(i)) * (sv - own) + dv;
+            a += n[k][i] - ld.dev(k, i, x, y);
+        }
+        acc[k] = own + a;
+    }
+    rr = acc[0];
+    rb = acc[1];
+    if (NEED_J) {
+        float m[9];
+#pragma unroll
+        for (int i = 1; i < 9; i++) m[i] = n[0][i] + n[1][i];
+        jx = (m[1] - m[3]) + (m[5] - m[7]) + (m[8] - m[6]);
+        jy = (m[2] - m[4]) + (m[5] - m[7]) + (m[6] - m[8]);
+    } else {
+        jx = jy = 0.0f;
+    }
+}
+
 // Pre-collision populations of both colours of node (x, y) at time t in FP64
 // (boundary conditions included), for state export.
 template <bool HERMITE, class Loader>
@@ -334,6 +389,12 @@ struct NodeMoments {
     float rr, rb, ux, uy, psi;
 };
 
+// Eq. (eq:color_field): psi = (rho_r / rho_r^0 - rho_b / rho_b^0) / (rho_r / rho_r^0 + rho_b / rho_b^0).
+__device__ __forceinline__ float colour_field(const Phys &p, float rr, float rb) {
+    const float a = rr * p.inv_gamma;
+    return (a - rb) / (a + rb);   // IEEE division: exactly +-1 in a pure phase
+}
+
 __device__ __forceinline__ NodeMoments node_moments(const Phys &p, const Pulled &P) {
     const float rho = P.rr + P.rb;
     const float jx = (P.e[1] - P.e[3]) + (P.e[5] - P.e[7]) + (P.e[8] - P.e[6]);
@@ -343,8 +404,7 @@ __device__ __forceinline__ NodeMoments node_moments(const Phys &p, const Pulled 
     m.rb = P.rb;
     m.ux = jx / rho + 0.5f * p.gx;   // Guo half-force shift
     m.uy = jy / rho + 0.5f * p.gy;
-    const float a = P.rr * p.inv_gamma;
-    m.psi = (a - P.rb) / (a + P.rb); // Eq. (eq:color_field)
+    m.psi = colour_field(p, P.rr, P.rb);
     return m;
 }
 
@@ -362,12 +422,12 @@ __device__ __forceinline__ float omega_eff(const Phys &p, float psi) {
 // post-collision deviations dr[1..8], db[1..8] of the stored state (the colour
 // densities are unchanged by the step's collision part).
 template <int CV>
-__device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, float Fx, float Fy, float dQx,
-                                             float dQy, float (&dr)[9], float (&db)[9]) {
+__device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, float psi, float Fx, float Fy,
+                                             float dQx, float dQy, float (&dr)[9], float (&db)[9]) {
     constexpr bool MRT = (CV & CV_MRT) != 0, HERMITE = (CV & CV_HERMITE) != 0;
     const float rr = P.rr, rb = P.rb;
     const float rho = rr + rb;
-    const float inv_rho = 1.0f / rho;
+    const float inv_rho = __fdividef(1.0f, rho);
     float e[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) e[i] = P.e[i];
@@ -375,9 +435,8 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
     const float jy = (e[2] - e[4]) + (e[5] - e[7]) + (e[6] - e[8]);
     const float ux = jx * inv_rho + 0.5f * p.gx;
     const float uy = jy * inv_rho + 0.5f * p.gy;
-    const float ca = rr * p.inv_gamma;
-    const float psi = (ca - rb) / (ca + rb);
     const float w = omega_eff(p, psi);
+    const bool force = (p.gx != 0.0f) || (p.gy != 0.0f);
 
     // velocity part of the colour-blind equilibrium, sum_k N^{k(e)}_i - R_i
     // (Eq. (eq:equilibrium) / (eq:equilibrium_hermite)), and the Guo source
@@ -393,7 +452,7 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
         if (HERMITE && C2(i) > 0) lin += 3.0f * cu * (3.0f * C2(i) - 4.0f) * herm;
         weq[i] = WT(i) * (lin + rho * (4.5f * cu * cu - 1.5f * usq));
         const float cG = CX(i) * Gx + CY(i) * Gy;
-        src[i] = WT(i) * (3.0f * (cG - uG) + 9.0f * cu * cG);
+        src[i] = force ? WT(i) * (3.0f * (cG - uG) + 9.0f * cu * cG) : 0.0f;
     }
 
     if (!MRT) {
@@ -462,8 +521,8 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
     const float F2 = Fx * Fx + Fy * Fy;
     if (F2 > 0.0f) {
         // Eq. (eq:perturbation), one A/2 term per colour: A |F| [W (F.c)^2/|F|^2 - B]
-        const float Fn = sqrtf(F2);
-        const float invFn = 1.0f / Fn;
+        const float invFn = rsqrtf(F2);
+        const float Fn = F2 * invFn;
         const float A = p.a_coef * w;
         const float pa = A * invFn, pb = A * Fn;
         const float kk = p.beta * mix * inv_rho * invFn;   // beta rr rb / rho^2 / |F|
@@ -515,6 +574,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // Plain arrival (no transaction bytes): completes the phase of a count-1 barrier.

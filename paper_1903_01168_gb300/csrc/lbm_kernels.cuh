@@ -117,20 +117,22 @@ struct FusedCfg {
     static_assert(RHO_BYTES % 128 == 0, "deviation block of a slot must stay 128-byte aligned");
 };
 
+// Persistent fused step.  Block b processes the work items
+// items[item_off[b] .. item_off[b+1]) in order (strip segments, possibly of
+// different simulations), so that every block gets an equal share of rows.
 template <typename T, int CV, int W, int NSLOT>
 __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__ descs,
-                                                     const WorkItem *__restrict__ items, int n_items,
+                                                     const WorkItem *__restrict__ items,
+                                                     const int *__restrict__ item_off, int n_blocks,
                                                      int step_offset, int *__restrict__ err) {
     using Cfg = FusedCfg<T, W, NSLOT>;
-    constexpr bool HERMITE_SRC = (CV & CV_MRT) && (CV & CV_HERMITE);
-    constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
     constexpr int G = Cfg::G, BOXW = Cfg::BOXW, RING = Cfg::RING;
+    constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
+    constexpr bool HERMITE_SRC = HERMITE && (CV & CV_MRT);
     extern __shared__ __align__(128) unsigned char smem[];
 
-    if ((int)blockIdx.x >= n_items) return;
+    if ((int)blockIdx.x >= n_blocks) return;
     const int tid = threadIdx.x;
-    const WorkItem it = items[blockIdx.x];
-    const SimDesc *gd = descs + it.sim;
 
     SimDesc &d = *reinterpret_cast<SimDesc *>(smem);
     unsigned char *slots = smem + Cfg::DESC_BYTES;
@@ -146,176 +148,187 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
         if (tid == 0) atomicOr(err, ERR_ALIGN);
         return;
     }
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(gd);
-        int4 *dst = reinterpret_cast<int4 *>(smem);
-        for (int j = tid; j < (int)(sizeof(SimDesc) / 16); j += W) dst[j] = src[j];
-    }
-    if (tid == 0) {
-        s_bad = 0;
-        for (int s = 0; s < NSLOT; s++) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-        fence_proxy_async_smem();
-        tensormap_acquire(&gd->tmap_rho);
-        tensormap_acquire(&gd->tmap_dev);
-    }
-    __syncthreads();
+    if (tid == 0) s_bad = 0;
 
-    const Phys p = d.ph;   // per-simulation constants, in registers from here on
-    const long long t = d.t0 + step_offset;
-    const int bsrc = (int)(t & 1), bdst = bsrc ^ 1;
-    const int nx = p.nx, ny = p.ny;
-    const bool wall_y = p.bc_y == BC_WALL;
-    const int x0 = it.x0, w = it.w, ya = it.ya, yb = it.yb;
-    if (d.variant != CV || w <= 0 || w > W || x0 < 0 || x0 + w > nx || (x0 % 8) != 0 || ya < 0 || yb > ny ||
-        ya >= yb) {
-        if (tid == 0) atomicOr(err, ERR_BADITEM);
-        return;
-    }
-    const int row_first = ya - 2, row_last = yb + 1;
-
-    auto row_valid = [&](int r) { return !wall_y || (r >= 0 && r < ny); };
-    auto slot_of = [&](int r) { return (r - row_first) % NSLOT; };
-    auto parity_of = [&](int r) { return (uint32_t)(((r - row_first) / NSLOT) & 1); };
-    auto row_ptr = [&](int r) { return slots + slot_of(r) * Cfg::SLOT_BYTES; };
-    // Load source row r (both colour densities and all 16 deviation planes) into
-    // its slot.  A row behind a wall is not loaded, but its slot barrier still
-    // completes one phase (plain arrival) so that every slot's phase parity
-    // stays (use count) & 1.
-    auto issue = [&](int r) {
-        const int s = slot_of(r);
-        if (!row_valid(r)) {
-            mbar_arrive(&bars[s]);
-            return;
+    const int it_end = item_off[blockIdx.x + 1];
+    for (int itx = item_off[blockIdx.x]; itx < it_end; ++itx) {
+        const WorkItem it = items[itx];
+        const SimDesc *gd = descs + it.sim;
+        __syncthreads();   // previous segment fully consumed (all its rows were waited for)
+        {
+            const int4 *src = reinterpret_cast<const int4 *>(gd);
+            int4 *dst = reinterpret_cast<int4 *>(smem);
+            for (int j = tid; j < (int)(sizeof(SimDesc) / 16); j += W) dst[j] = src[j];
         }
-        const int yr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
-        unsigned char *dst = slots + s * Cfg::SLOT_BYTES;
-        mbar_arrive_expect_tx(&bars[s], Cfg::TX_BYTES);
-        // box origin: column x0 - G of the row = element x0 of the padded row
-        tma_load_3d(dst, &gd->tmap_rho, &bars[s], x0, yr, bsrc * 2);
-        tma_load_3d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], x0, yr, bsrc * 16);
-    };
-    int next_issue = row_first;   // meaningful on thread 0 only
-    if (tid == 0) {
-        for (; next_issue <= row_last && next_issue < row_first + NSLOT; ++next_issue) issue(next_issue);
-    }
-
-    bool ok = true;
-    auto wait_row = [&](int r) {
-        if (ok && r <= row_last && row_valid(r)) {
-            if (!mbar_wait_bounded(&bars[slot_of(r)], parity_of(r), WAIT_LIMIT_CYCLES)) {
-                ok = false;
-                s_bad = 1;
+        if (tid == 0) {
+            for (int s = 0; s < NSLOT; s++) {
+                if (itx != item_off[blockIdx.x]) mbar_inval(&bars[s]);
+                mbar_init(&bars[s], 1);
             }
+            fence_mbar_init();
+            fence_proxy_async_smem();
+            tensormap_acquire(&gd->tmap_rho);
+            tensormap_acquire(&gd->tmap_dev);
         }
-    };
-    auto loader = [&](int y) {
-        SmemLoader<T, BOXW, G> L;
-        L.r0 = row_ptr(y - 1);
-        L.r1 = row_ptr(y);
-        L.r2 = row_ptr(y + 1);
-        L.y = y;
-        L.x0 = x0;
-        return L;
-    };
+        __syncthreads();
 
-    // colour field, colour densities (and q u) of ring row Y, columns x0-1 .. x0+w
-    auto stageA = [&](int Y) {
-        const int rs = ((Y + 4) & 3) * RING;
-        if (wall_y && (Y < 0 || Y >= ny)) {
-            const int Yn = Y < 0 ? 0 : ny - 1;
-            const auto L = loader(Yn);
-            for (int c = tid; c < w + 2; c += W) {
-                const int X = x0 - 1 + c;
-                const float ps = wall_psi(p, X, [&](int Xp) {
-                    Pulled P;
-                    pull_node<HERMITE>(p, L, Xp, Yn, t, false, 0.0f, 0.0f, P);
-                    return node_moments(p, P).psi;
-                });
-                ring_psi[rs + c] = ps;
-                ring_qx[rs + c] = 0.0f;
-                ring_qy[rs + c] = 0.0f;
+        const Phys p = d.ph;   // per-simulation constants, in registers from here on
+        const long long t = d.t0 + step_offset;
+        const int bsrc = (int)(t & 1), bdst = bsrc ^ 1;
+        const int nx = p.nx, ny = p.ny;
+        const bool wall_y = p.bc_y == BC_WALL;
+        const int x0 = it.x0, w = it.w, ya = it.ya, yb = it.yb;
+        if (d.variant != CV || w <= 0 || w > W || x0 < 0 || x0 + w > nx || (x0 % 8) != 0 || ya < 0 || yb > ny ||
+            ya >= yb) {
+            if (tid == 0) atomicOr(err, ERR_BADITEM);
+            continue;
+        }
+        const int row_first = ya - 2, row_last = yb + 1;
+
+        auto row_valid = [&](int r) { return !wall_y || (r >= 0 && r < ny); };
+        auto slot_of = [&](int r) { return (r - row_first) % NSLOT; };
+        auto parity_of = [&](int r) { return (uint32_t)(((r - row_first) / NSLOT) & 1); };
+        auto row_ptr = [&](int r) { return slots + slot_of(r) * Cfg::SLOT_BYTES; };
+        // Load source row r (both colour densities and all 16 deviation planes)
+        // into its slot.  A row behind a wall is not loaded, but its slot barrier
+        // still completes one phase (plain arrival) so that every slot's phase
+        // parity stays (use count) & 1.
+        auto issue = [&](int r) {
+            const int s = slot_of(r);
+            if (!row_valid(r)) {
+                mbar_arrive(&bars[s]);
+                return;
             }
-        } else {
-            const auto L = loader(Y);
-            for (int c = tid; c < w + 2; c += W) {
-                int X = x0 - 1 + c;
-                if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
-                Pulled P;
-                pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
-                const NodeMoments m = node_moments(p, P);
-                ring_psi[rs + c] = m.psi;
-                ring_rr[rs + c] = m.rr;
-                ring_rb[rs + c] = m.rb;
-                if (HERMITE_SRC) {
-                    const float q = p.q_r * m.rr + p.q_b * m.rb;
-                    ring_qx[rs + c] = q * m.ux;
-                    ring_qy[rs + c] = q * m.uy;
+            const int yr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
+            unsigned char *dst = slots + s * Cfg::SLOT_BYTES;
+            mbar_arrive_expect_tx(&bars[s], Cfg::TX_BYTES);
+            // box origin: column x0 - G of the row = element x0 of the padded row
+            tma_load_3d(dst, &gd->tmap_rho, &bars[s], x0, yr, bsrc * 2);
+            tma_load_3d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], x0, yr, bsrc * 16);
+        };
+        int next_issue = row_first;   // meaningful on thread 0 only
+        if (tid == 0) {
+            for (; next_issue <= row_last && next_issue < row_first + NSLOT; ++next_issue) issue(next_issue);
+        }
+
+        bool ok = true;
+        auto wait_row = [&](int r) {
+            if (ok && r <= row_last && row_valid(r)) {
+                if (!mbar_wait_bounded(&bars[slot_of(r)], parity_of(r), WAIT_LIMIT_CYCLES)) {
+                    ok = false;
+                    s_bad = 1;
                 }
             }
-        }
-    };
-
-    auto stageB = [&](int y) {
-        if (tid >= w) return;
-        const int x = x0 + tid;
-        const int rm = ((y + 3) & 3) * RING, r0 = ((y + 4) & 3) * RING, rp = ((y + 5) & 3) * RING;
-        const int c = tid + 1;
-        Pulled P;
-        pull_node<HERMITE>(p, loader(y), x, y, t, true, ring_rr[r0 + c], ring_rb[r0 + c], P);
-        auto ring = [&](const float *f) {
-            return [=](int dx, int dy) { return f[(dy < 0 ? rm : (dy == 0 ? r0 : rp)) + c + dx]; };
         };
-        float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
-        s2i4(ring(ring_psi), Fx, Fy);
-        if (HERMITE_SRC) {
-            float gx_, gy_;
-            s2i4(ring(ring_qx), dQx, gy_);
-            s2i4(ring(ring_qy), gx_, dQy);
-        }
-        float dr[9], db[9];
-        collide_node<CV>(p, P, Fx, Fy, dQx, dQy, dr, db);
-        NodeStore<T>(d, p, bdst, x, y).store(P.rr, P.rb, dr, db);
-    };
+        auto loader = [&](int y) {
+            SmemLoader<T, BOXW, G> L;
+            L.r0 = row_ptr(y - 1);
+            L.r1 = row_ptr(y);
+            L.r2 = row_ptr(y + 1);
+            L.y = y;
+            L.x0 = x0;
+            return L;
+        };
 
-    // prologue: ring rows ya and ya - 1
-    wait_row(ya - 1);
-    wait_row(ya);
-    wait_row(ya + 1);
-    stageA(ya);
-    wait_row(ya - 2);
-    stageA(ya - 1);
-
-    for (int y = ya; y < yb; ++y) {
-        wait_row(y + 2);
-        stageA(y + 1);
-        __syncthreads();
-        if (s_bad) break;
-        if (tid == 0) {
-            const int r = y - 2 + NSLOT;
-            if (r == next_issue && r <= row_last) {
-                issue(r);
-                ++next_issue;
+        // colour field, colour densities (and q u) of ring row Y, columns x0-1 .. x0+w
+        auto stageA = [&](int Y) {
+            const int rs = ((Y + 4) & 3) * RING;
+            if (wall_y && (Y < 0 || Y >= ny)) {
+                const int Yn = Y < 0 ? 0 : ny - 1;
+                const auto L = loader(Yn);
+                for (int c = tid; c < w + 2; c += W) {
+                    const int X = x0 - 1 + c;
+                    const float ps = wall_psi(p, X, [&](int Xp) {
+                        float rr, rb, jx, jy;
+                        pull_moments<HERMITE, false>(p, L, Xp, Yn, t, rr, rb, jx, jy);
+                        return colour_field(p, rr, rb);
+                    });
+                    ring_psi[rs + c] = ps;
+                    ring_qx[rs + c] = 0.0f;
+                    ring_qy[rs + c] = 0.0f;
+                }
+            } else {
+                const auto L = loader(Y);
+                for (int c = tid; c < w + 2; c += W) {
+                    int X = x0 - 1 + c;
+                    if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
+                    float rr, rb, jx, jy;
+                    pull_moments<HERMITE, HERMITE_SRC>(p, L, X, Y, t, rr, rb, jx, jy);
+                    ring_psi[rs + c] = colour_field(p, rr, rb);
+                    ring_rr[rs + c] = rr;
+                    ring_rb[rs + c] = rb;
+                    if (HERMITE_SRC) {
+                        const float rho = rr + rb;
+                        const float q = p.q_r * rr + p.q_b * rb;
+                        ring_qx[rs + c] = q * (jx / rho + 0.5f * p.gx);
+                        ring_qy[rs + c] = q * (jy / rho + 0.5f * p.gy);
+                    }
+                }
             }
-        }
-        stageB(y);
-    }
+        };
 
-    if (s_bad) {
-        __syncthreads();
-        if (tid == 0) {
-            atomicOr(err, ERR_TIMEOUT);
-            // wait (bounded) for the copies this block still has in flight, so
-            // that none lands after the block's shared memory is released: the
-            // latest phase issued into each slot covers the earlier ones
-            for (int s = 0; s < NSLOT; s++) {
-                int last = -1 << 30;
-                for (int r = row_first; r < next_issue; ++r)
-                    if (slot_of(r) == s) last = r;
-                if (last > (-1 << 30)) mbar_wait_bounded(&bars[s], parity_of(last), WAIT_LIMIT_CYCLES / 4);
+        auto stageB = [&](int y) {
+            if (tid >= w) return;
+            const int x = x0 + tid;
+            const int rm = ((y + 3) & 3) * RING, r0 = ((y + 4) & 3) * RING, rp = ((y + 5) & 3) * RING;
+            const int c = tid + 1;
+            Pulled P;
+            pull_node<HERMITE>(p, loader(y), x, y, t, true, ring_rr[r0 + c], ring_rb[r0 + c], P);
+            auto ring = [&](const float *f) {
+                return [=](int dx, int dy) { return f[(dy < 0 ? rm : (dy == 0 ? r0 : rp)) + c + dx]; };
+            };
+            float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
+            s2i4(ring(ring_psi), Fx, Fy);
+            if (HERMITE_SRC) {
+                float gx_, gy_;
+                s2i4(ring(ring_qx), dQx, gy_);
+                s2i4(ring(ring_qy), gx_, dQy);
             }
+            float dr[9], db[9];
+            collide_node<CV>(p, P, ring_psi[r0 + c], Fx, Fy, dQx, dQy, dr, db);
+            NodeStore<T>(d, p, bdst, x, y).store(P.rr, P.rb, dr, db);
+        };
+
+        // prologue: ring rows ya and ya - 1
+        wait_row(ya - 1);
+        wait_row(ya);
+        wait_row(ya + 1);
+        stageA(ya);
+        wait_row(ya - 2);
+        stageA(ya - 1);
+
+        for (int y = ya; y < yb; ++y) {
+            wait_row(y + 2);
+            stageA(y + 1);
+            __syncthreads();
+            if (s_bad) break;
+            if (tid == 0) {
+                const int r = y - 2 + NSLOT;
+                if (r == next_issue && r <= row_last) {
+                    issue(r);
+                    ++next_issue;
+                }
+            }
+            stageB(y);
         }
-        __syncthreads();
+
+        if (s_bad) {
+            __syncthreads();
+            if (tid == 0) {
+                atomicOr(err, ERR_TIMEOUT);
+                // wait (bounded) for the copies this block still has in flight, so
+                // that none lands after the block's shared memory is released: the
+                // latest phase issued into each slot covers the earlier ones
+                for (int s = 0; s < NSLOT; s++) {
+                    int last = -1 << 30;
+                    for (int r = row_first; r < next_issue; ++r)
+                        if (slot_of(r) == s) last = r;
+                    if (last > (-1 << 30)) mbar_wait_bounded(&bars[s], parity_of(last), WAIT_LIMIT_CYCLES / 4);
+                }
+            }
+            __syncthreads();
+            return;
+        }
     }
 }
 
@@ -397,7 +410,7 @@ __global__ void k_tp_collide(const SimDesc *__restrict__ dp, int step_offset, co
             s2i4([&](int dx, int dy) { return aux_at(p, aux + 4 * n, x + dx, y + dy, false); }, gx_, dQy);
         }
         float dr[9], db[9];
-        collide_node<CV>(p, P, Fx, Fy, dQx, dQy, dr, db);
+        collide_node<CV>(p, P, aux[k], Fx, Fy, dQx, dQy, dr, db);
         NodeStore<T>(d, p, bsrc ^ 1, x, y).store(P.rr, P.rb, dr, db);
     }
 }

