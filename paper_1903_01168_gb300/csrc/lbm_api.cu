@@ -24,7 +24,7 @@ using namespace lbm;
 namespace {
 
 constexpr int FUSED_W = 128;     // columns per strip = threads per block
-constexpr int FUSED_NSLOT = 6;   // shared-memory row slots per block
+constexpr int FUSED_NSLOT = 5;   // shared-memory row slots per block
 
 thread_local char g_create_err[256] = "";
 
@@ -57,9 +57,9 @@ const void *fused_kernel_ptr() {
     return reinterpret_cast<const void *>(&k_step_fused<T, CV, FUSED_W, FUSED_NSLOT>);
 }
 
-template <typename T>
+template <typename T, int CV>
 int fused_smem() {
-    return FusedCfg<T, FUSED_W, FUSED_NSLOT>::SMEM;
+    return FusedCfg<T, CV, FUSED_W, FUSED_NSLOT>::SMEM;
 }
 
 int variant_of(const lbm_params *p) {
@@ -244,7 +244,7 @@ lbm_status encode_tmap(lbm_sim *s) {
     const CUtensorMapDataType dt = s->p.storage == ST_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : s->p.storage == ST_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const cuuint32_t box_w = FUSED_W + 2 * GHOST;
+    const cuuint32_t box_w = FUSED_W + 2 * (16 / es);   // halo columns loaded: 4 (FP32) or 8 (16-bit)
     cuuint32_t estr[3] = {1, 1, 1};
     {
         cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch_r, (cuuint64_t)s->ny, 4};
@@ -252,7 +252,7 @@ lbm_status encode_tmap(lbm_sim *s) {
         cuuint32_t box[3] = {box_w, 1, 2};
         CUresult r = enc(&s->h.tmap_rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->h.rho, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { set_err(s->err, "cuTensorMapEncodeTiled (rho) failed (%d)", (int)r); return LBM_ECUDA; }
     }
     {
@@ -260,7 +260,7 @@ lbm_status encode_tmap(lbm_sim *s) {
         cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch_d * es, (cuuint64_t)s->h.dev_plane * es};
         cuuint32_t box[3] = {box_w, 1, 16};
         CUresult r = enc(&s->h.tmap_dev, dt, 3, s->h.dev, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { set_err(s->err, "cuTensorMapEncodeTiled (dev) failed (%d)", (int)r); return LBM_ECUDA; }
     }
@@ -360,11 +360,11 @@ cudaError_t launch_fused_t(const SimDesc *descs, const WorkItem *items, const in
     cudaGetDevice(&dev);
     if (dev < 64 && !attr_done[dev]) {
         cudaError_t e = cudaFuncSetAttribute(fused_kernel_ptr<T, CV>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             fused_smem<T>());
+                                             fused_smem<T, CV>());
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
-    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_blocks, FUSED_W, fused_smem<T>(), st>>>(descs, items, item_off,
+    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_blocks, FUSED_W, fused_smem<T, CV>(), st>>>(descs, items, item_off,
                                                                                        n_blocks, off, err);
     return cudaGetLastError();
 }
@@ -396,10 +396,11 @@ int resident_blocks(int storage) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void *k = storage == ST_F32 ? fused_kernel_ptr<float, 0>()
-                    : storage == ST_F16DEV ? fused_kernel_ptr<__half, 0>() : fused_kernel_ptr<__nv_bfloat16, 0>();
-    const int smem = storage == ST_F32 ? fused_smem<float>() : storage == ST_F16DEV ? fused_smem<__half>()
-                                                                                     : fused_smem<__nv_bfloat16>();
+    const void *k = storage == ST_F32 ? fused_kernel_ptr<float, 3>()
+                    : storage == ST_F16DEV ? fused_kernel_ptr<__half, 3>() : fused_kernel_ptr<__nv_bfloat16, 3>();
+    // the largest variant (MRT + Hermite source rings) bounds the residency of all
+    const int smem = storage == ST_F32 ? fused_smem<float, 3>() : storage == ST_F16DEV ? fused_smem<__half, 3>()
+                                                                                        : fused_smem<__nv_bfloat16, 3>();
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, FUSED_W, smem) != cudaSuccess || per < 1) per = 1;
     if (sms < 1) sms = 1;

@@ -451,8 +451,15 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
         float lin = rho * 3.0f * cu;
         if (HERMITE && C2(i) > 0) lin += 3.0f * cu * (3.0f * C2(i) - 4.0f) * herm;
         weq[i] = WT(i) * (lin + rho * (4.5f * cu * cu - 1.5f * usq));
-        const float cG = CX(i) * Gx + CY(i) * Gy;
-        src[i] = force ? WT(i) * (3.0f * (cG - uG) + 9.0f * cu * cG) : 0.0f;
+        src[i] = 0.0f;
+    }
+    if (force) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const float cu = CX(i) * ux + CY(i) * uy;
+            const float cG = CX(i) * Gx + CY(i) * Gy;
+            src[i] = WT(i) * (3.0f * (cG - uG) + 9.0f * cu * cG);
+        }
     }
 
     if (!MRT) {

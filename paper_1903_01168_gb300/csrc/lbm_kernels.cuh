@@ -50,8 +50,9 @@ struct GlobalLoader {
 };
 
 // Stored values from the shared-memory row ring (rows y-1, y, y+1 of a strip
-// starting at column x0).  A slot holds [2][BOXW] floats then [16][BOXW] T.
-template <typename T, int BOXW, int G>
+// starting at column x0).  A slot holds [2][BOXW] floats (padded to RHO_BYTES)
+// then [16][BOXW] T.
+template <typename T, int BOXW, int G, int RHO_BYTES>
 struct SmemLoader {
     const unsigned char *r0, *r1, *r2;
     int y, x0;
@@ -63,9 +64,12 @@ struct SmemLoader {
         return reinterpret_cast<const float *>(row(ys))[k * BOXW + (xs - x0 + G)];
     }
     __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
-        const T *p = reinterpret_cast<const T *>(row(ys) + 2 * BOXW * sizeof(float));
+        const T *p = reinterpret_cast<const T *>(row(ys) + RHO_BYTES);
         return Codec<T>::dec(p[(k * 8 + i - 1) * BOXW + (xs - x0 + G)]);
     }
+    // same, for direction indices known only at run time
+    __device__ __forceinline__ float rho_rt(int k, int xs, int ys) const { return rho(k, xs, ys); }
+    __device__ __forceinline__ float dev_rt(int k, int i, int xs, int ys) const { return dev(k, i, xs, ys); }
 };
 
 // psi on a solid wall row: W-weighted mean of the in-domain fluid nodes next
@@ -97,38 +101,83 @@ __device__ __forceinline__ void s2i4(const V &v, float &gx, float &gy) {
     gy = (1.0f / 3.0f) * (n - s) + (1.0f / 12.0f) * (a - b);
 }
 
+// Colour densities of one pulled node computed by 16 lanes of a warp: lane
+// j = 8 k + (i - 1) adds colour k's direction-i term of
+//   rho_k' = rho_k(x) + sum_{i>=1} [phi^k_i (s^k_i - rho_k(x)) + delta^k_i - d^k_i(x)]
+// and the two colour sums are reduced with shuffles inside the 16-lane group.
+// No wall link may touch the node (callers use the serial pull next to walls).
+template <class Loader>
+__device__ __forceinline__ void pull_rho_coop16(const Phys &p, const Loader &ld, int x, int y, int j, float &rr,
+                                                float &rb) {
+    const int k = j >> 3, i = (j & 7) + 1;
+    const int cx = (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+    const int cy = (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+    const int c2 = cx * cx + cy * cy;
+    const float ph = k == 0 ? (c2 == 1 ? p.phi_r[1] : p.phi_r[2]) : (c2 == 1 ? p.phi_b[1] : p.phi_b[2]);
+    const float own = ld.rho_rt(k, x, y);
+    float v = ph * (ld.rho_rt(k, x - cx, y - cy) - own) + (ld.dev_rt(k, i, x - cx, y - cy) - ld.dev_rt(k, i, x, y));
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    const float mine = own + v;                        // colour k's new density
+    const float other = __shfl_xor_sync(0xffffffffu, mine, 8);
+    rr = k == 0 ? mine : other;
+    rb = k == 0 ? other : mine;
+}
+
 // ------------------------------------------------------------ fused kernel
 
-template <typename T, int W, int NSLOT>
+template <typename T, int CV, int W, int NSLOT>
 struct FusedCfg {
-    static constexpr int G = 8;                              // ghost columns each side
+    static constexpr int GMEM = 8;                           // ghost columns kept in memory
+    static constexpr int G = 16 / (int)sizeof(T);            // halo columns loaded each side
     static constexpr int BOXW = W + 2 * G;                   // TMA box width (elements)
-    static constexpr int RHO_BYTES = 2 * BOXW * 4;
+    static constexpr int RHO_BYTES = ((2 * BOXW * 4 + 127) / 128) * 128;
     static constexpr int DEV_BYTES = 16 * BOXW * (int)sizeof(T);
     static constexpr int SLOT_BYTES = ((RHO_BYTES + DEV_BYTES + 127) / 128) * 128;
     static constexpr int RING = W + 2;                       // ring width (columns x0-1 .. x0+W)
-    static constexpr int NRING = 5;                          // psi, rho_r, rho_b, q ux, q uy
+    static constexpr bool QRING = (CV & CV_MRT) && (CV & CV_HERMITE);
+    // shared rings (floats).  Stage A of row y+1 may run while slower threads
+    // still do stage B of row y-1, so a ring written by A and read by B for
+    // its own row needs 3 rows (rho_r, rho_b, e_1..8), and one read over rows
+    // y-1..y+1 needs 4 (psi, q u).
+    static constexpr int PSI_OFF = 0;
+    static constexpr int RR_OFF = PSI_OFF + 4 * RING;
+    static constexpr int RB_OFF = RR_OFF + 3 * RING;
+    static constexpr int E_OFF = RB_OFF + 3 * RING;
+    static constexpr int QX_OFF = E_OFF + 3 * 8 * RING;
+    static constexpr int QY_OFF = QX_OFF + (QRING ? 4 * RING : 0);
+    static constexpr int RING_FLOATS = QY_OFF + (QRING ? 4 * RING : 0);
     static constexpr int DESC_BYTES = ((int)sizeof(SimDesc) + 127) / 128 * 128;
-    static constexpr int RING_BYTES = NRING * 4 * RING * 4;
+    static constexpr int RING_BYTES = ((RING_FLOATS * 4 + 15) / 16) * 16;
     static constexpr int SMEM = DESC_BYTES + NSLOT * SLOT_BYTES + RING_BYTES + NSLOT * 8 + 16;
-    static constexpr uint32_t TX_BYTES = (uint32_t)(RHO_BYTES + DEV_BYTES);
+    static constexpr uint32_t TX_BYTES = (uint32_t)(2 * BOXW * 4 + DEV_BYTES);
     static_assert(BOXW <= 256, "TMA box dimension limit");
     static_assert((BOXW * sizeof(T)) % 16 == 0 && (BOXW * 4) % 16 == 0, "TMA inner box bytes");
-    static_assert(RHO_BYTES % 128 == 0, "deviation block of a slot must stay 128-byte aligned");
+    static_assert(G <= GMEM && G >= 3, "halo must cover the stencil and fit the memory ghost");
 };
 
 // Persistent fused step.  Block b processes the work items
 // items[item_off[b] .. item_off[b+1]) in order (strip segments, possibly of
 // different simulations), so that every block gets an equal share of rows.
+//
+// Per segment the block marches up rows ya .. yb-1 of a strip of w <= W
+// columns.  Source rows arrive by TMA into a ring of NSLOT shared slots.
+// Iteration y first pulls ring row y+1 (stage A: new colour densities, colour
+// field and the colour-blind non-rest parts e_i of every node of that row, plus
+// one column each side), then collides row y (stage B) from what stage A left
+// in the shared rings: its own densities and e_i, and the colour field of rows
+// y-1..y+1 for the S2I4 gradient.  Stage B reads no source row, so a row's slot
+// is refilled as soon as stage A of the row above has used it.
 template <typename T, int CV, int W, int NSLOT>
 __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__ descs,
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ item_off, int n_blocks,
                                                      int step_offset, int *__restrict__ err) {
-    using Cfg = FusedCfg<T, W, NSLOT>;
+    using Cfg = FusedCfg<T, CV, W, NSLOT>;
     constexpr int G = Cfg::G, BOXW = Cfg::BOXW, RING = Cfg::RING;
     constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
-    constexpr bool HERMITE_SRC = HERMITE && (CV & CV_MRT);
+    constexpr bool HERMITE_SRC = Cfg::QRING;
     extern __shared__ __align__(128) unsigned char smem[];
 
     if ((int)blockIdx.x >= n_blocks) return;
@@ -136,12 +185,14 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
 
     SimDesc &d = *reinterpret_cast<SimDesc *>(smem);
     unsigned char *slots = smem + Cfg::DESC_BYTES;
-    float *ring_psi = reinterpret_cast<float *>(slots + NSLOT * Cfg::SLOT_BYTES);
-    float *ring_rr = ring_psi + 4 * RING;
-    float *ring_rb = ring_rr + 4 * RING;
-    float *ring_qx = ring_rb + 4 * RING;
-    float *ring_qy = ring_qx + 4 * RING;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(ring_qy + 4 * RING);
+    float *rings = reinterpret_cast<float *>(slots + NSLOT * Cfg::SLOT_BYTES);
+    float *ring_psi = rings + Cfg::PSI_OFF;
+    float *ring_rr = rings + Cfg::RR_OFF;
+    float *ring_rb = rings + Cfg::RB_OFF;
+    float *ring_e = rings + Cfg::E_OFF;
+    float *ring_qx = rings + Cfg::QX_OFF;
+    float *ring_qy = rings + Cfg::QY_OFF;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(rings) + Cfg::RING_BYTES);
     volatile int &s_bad = *reinterpret_cast<volatile int *>(bars + NSLOT);
 
     if (smem_u32(slots) & 127) {   // TMA destinations must be 128-byte aligned
@@ -178,8 +229,8 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
         const int nx = p.nx, ny = p.ny;
         const bool wall_y = p.bc_y == BC_WALL;
         const int x0 = it.x0, w = it.w, ya = it.ya, yb = it.yb;
-        if (d.variant != CV || w <= 0 || w > W || x0 < 0 || x0 + w > nx || (x0 % 8) != 0 || ya < 0 || yb > ny ||
-            ya >= yb) {
+        if (d.variant != CV || d.ghost != Cfg::GMEM || w <= 0 || w > W || x0 < 0 || x0 + w > nx || (x0 % 8) != 0 ||
+            ya < 0 || yb > ny || ya >= yb) {
             if (tid == 0) atomicOr(err, ERR_BADITEM);
             continue;
         }
@@ -189,10 +240,10 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
         auto slot_of = [&](int r) { return (r - row_first) % NSLOT; };
         auto parity_of = [&](int r) { return (uint32_t)(((r - row_first) / NSLOT) & 1); };
         auto row_ptr = [&](int r) { return slots + slot_of(r) * Cfg::SLOT_BYTES; };
-        // Load source row r (both colour densities and all 16 deviation planes)
-        // into its slot.  A row behind a wall is not loaded, but its slot barrier
-        // still completes one phase (plain arrival) so that every slot's phase
-        // parity stays (use count) & 1.
+        // Load source row r (both colour densities and all 16 deviation planes,
+        // columns x0-G .. x0+W+G-1) into its slot.  A row behind a wall is not
+        // loaded, but its slot barrier still completes one phase (plain arrival)
+        // so that every slot's phase parity stays (use count) & 1.
         auto issue = [&](int r) {
             const int s = slot_of(r);
             if (!row_valid(r)) {
@@ -201,10 +252,10 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
             }
             const int yr = r < 0 ? r + ny : (r >= ny ? r - ny : r);
             unsigned char *dst = slots + s * Cfg::SLOT_BYTES;
+            const int xb = x0 + (Cfg::GMEM - G);   // element index of column x0 - G in the padded row
             mbar_arrive_expect_tx(&bars[s], Cfg::TX_BYTES);
-            // box origin: column x0 - G of the row = element x0 of the padded row
-            tma_load_3d(dst, &gd->tmap_rho, &bars[s], x0, yr, bsrc * 2);
-            tma_load_3d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], x0, yr, bsrc * 16);
+            tma_load_3d(dst, &gd->tmap_rho, &bars[s], xb, yr, bsrc * 2);
+            tma_load_3d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], xb, yr, bsrc * 16);
         };
         int next_issue = row_first;   // meaningful on thread 0 only
         if (tid == 0) {
@@ -221,7 +272,7 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
             }
         };
         auto loader = [&](int y) {
-            SmemLoader<T, BOXW, G> L;
+            SmemLoader<T, BOXW, G, Cfg::RHO_BYTES> L;
             L.r0 = row_ptr(y - 1);
             L.r1 = row_ptr(y);
             L.r2 = row_ptr(y + 1);
@@ -230,7 +281,7 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
             return L;
         };
 
-        // colour field, colour densities (and q u) of ring row Y, columns x0-1 .. x0+w
+        // stage A: ring row Y, columns x0-1 .. x0+w
         auto stageA = [&](int Y) {
             const int rs = ((Y + 4) & 3) * RING;
             if (wall_y && (Y < 0 || Y >= ny)) {
@@ -244,36 +295,82 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
                         return colour_field(p, rr, rb);
                     });
                     ring_psi[rs + c] = ps;
-                    ring_qx[rs + c] = 0.0f;
-                    ring_qy[rs + c] = 0.0f;
+                    if (HERMITE_SRC) {
+                        ring_qx[rs + c] = 0.0f;
+                        ring_qy[rs + c] = 0.0f;
+                    }
                 }
             } else {
                 const auto L = loader(Y);
-                for (int c = tid; c < w + 2; c += W) {
+                const int m3 = (Y + 3) % 3;   // Y >= -1
+                const int r2 = m3 * RING, e2 = m3 * 8 * RING;
+                // interior ring columns x0 .. x0+w-1: one node per thread, full pull
+                if (tid < w) {
+                    const int c = tid + 1;
+                    const int X = x0 + tid;
+                    Pulled P;
+                    pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                    ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
+                    ring_rr[r2 + c] = P.rr;
+                    ring_rb[r2 + c] = P.rb;
+#pragma unroll
+                    for (int i = 1; i < 9; i++) ring_e[e2 + (i - 1) * RING + c] = P.e[i];
+                    if (HERMITE_SRC) {
+                        const NodeMoments m = node_moments(p, P);
+                        const float q = p.q_r * m.rr + p.q_b * m.rb;
+                        ring_qx[rs + c] = q * m.ux;
+                        ring_qy[rs + c] = q * m.uy;
+                    }
+                }
+                // the two edge columns x0-1 and x0+w only need psi (and q u): the
+                // last warp computes them 16 lanes per node, unless a boundary
+                // touches them (open column, wall row) or the node needs q u
+                const int Ye = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
+                const bool edge_plain = !HERMITE_SRC && p.bc_x == BC_PERIODIC &&
+                                        !(wall_y && (Ye == 0 || Ye == ny - 1));
+                if (edge_plain) {
+                    if (tid >= W - 32) {
+                        const int lane = tid & 31, e = lane >> 4;
+                        const int X = e == 0 ? x0 - 1 : x0 + w;
+                        float rr, rb;
+                        pull_rho_coop16(p, L, X, Y, lane & 15, rr, rb);
+                        if ((lane & 15) == 0) ring_psi[rs + (e == 0 ? 0 : w + 1)] = colour_field(p, rr, rb);
+                    }
+                } else if (tid < 2) {
+                    const int c = tid == 0 ? 0 : w + 1;
                     int X = x0 - 1 + c;
                     if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
-                    float rr, rb, jx, jy;
-                    pull_moments<HERMITE, HERMITE_SRC>(p, L, X, Y, t, rr, rb, jx, jy);
-                    ring_psi[rs + c] = colour_field(p, rr, rb);
-                    ring_rr[rs + c] = rr;
-                    ring_rb[rs + c] = rb;
+                    Pulled P;
+                    pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                    ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
                     if (HERMITE_SRC) {
-                        const float rho = rr + rb;
-                        const float q = p.q_r * rr + p.q_b * rb;
-                        ring_qx[rs + c] = q * (jx / rho + 0.5f * p.gx);
-                        ring_qy[rs + c] = q * (jy / rho + 0.5f * p.gy);
+                        const NodeMoments m = node_moments(p, P);
+                        const float q = p.q_r * m.rr + p.q_b * m.rb;
+                        ring_qx[rs + c] = q * m.ux;
+                        ring_qy[rs + c] = q * m.uy;
                     }
                 }
             }
         };
 
+        // stage B: collide row y from the rings
         auto stageB = [&](int y) {
             if (tid >= w) return;
             const int x = x0 + tid;
             const int rm = ((y + 3) & 3) * RING, r0 = ((y + 4) & 3) * RING, rp = ((y + 5) & 3) * RING;
             const int c = tid + 1;
+            const int m3 = (y + 3) % 3;
+            const int r2 = m3 * RING, e2 = m3 * 8 * RING;
             Pulled P;
-            pull_node<HERMITE>(p, loader(y), x, y, t, true, ring_rr[r0 + c], ring_rb[r0 + c], P);
+            P.rr = ring_rr[r2 + c];
+            P.rb = ring_rb[r2 + c];
+            float e0 = 0.0f;
+#pragma unroll
+            for (int i = 1; i < 9; i++) {
+                P.e[i] = ring_e[e2 + (i - 1) * RING + c];
+                e0 += P.e[i];
+            }
+            P.e[0] = -e0;
             auto ring = [&](const float *f) {
                 return [=](int dx, int dy) { return f[(dy < 0 ? rm : (dy == 0 ? r0 : rp)) + c + dx]; };
             };
@@ -303,11 +400,8 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
             __syncthreads();
             if (s_bad) break;
             if (tid == 0) {
-                const int r = y - 2 + NSLOT;
-                if (r == next_issue && r <= row_last) {
-                    issue(r);
-                    ++next_issue;
-                }
+                // rows <= y are no longer read (stage A(y+1) was their last reader)
+                for (; next_issue <= row_last && next_issue <= y + NSLOT; ++next_issue) issue(next_issue);
             }
             stageB(y);
         }
