@@ -190,6 +190,33 @@ const char *lbm_last_error(const lbm_sim *s);
 /* Free the simulation (its own buffers and stream; never caller memory). */
 void lbm_destroy(lbm_sim *s);
 
+/* ---- allocation-free stepping ---- */
+
+/* Advance n >= 0 steps of a simulation whose state lives in caller-owned device
+ * memory, allocating nothing: no cudaMalloc, cudaMallocAsync, cudaFree or
+ * allocating library routine is called.  The paper has no counterpart; this is
+ * for callers that cannot allocate device memory themselves at run time (an
+ * embedding runtime whose allocator owns the GPU, a fixed pre-registered memory
+ * pool, an allocation-free real-time loop).
+ *   p, nx, ny    parameters and lattice, as for lbm_create (p->kernel is ignored:
+ *                the two-pass kernels run); nx * ny <= 262144
+ *   state        device buffer of lbm_bytes_required(nx, ny, p) bytes, 256-byte
+ *                aligned, holding the state at time t in the layout of
+ *                lbm_save_state (its bytes after the leading time stamp); it is
+ *                advanced in place (the state at t + n ends in the same buffer)
+ *   t            time step of the state in `state`
+ *   cuda_stream  stream the kernels are queued on (asynchronous)
+ * The intermediate colour-field pass uses a static scratch array of 5 MiB that
+ * every GPU loading the library holds until exit.  Its device address is looked
+ * up by the first call made on each device, with that device current; make that
+ * first call before capturing any stream.  All calls share that one scratch and
+ * it keeps the previous call's contents: calls that may overlap on the GPU
+ * (different streams, or different simulations on one stream that are not
+ * ordered) race, so order them.  Lattices above 262144 nodes are rejected with
+ * LBM_EINVAL and a message in lbm_last_error(NULL). */
+lbm_status lbm_step_noalloc(const lbm_params *p, int nx, int ny, void *state, size_t bytes, long long t,
+                            long n, void *cuda_stream);
+
 /* ---- batched stepping of many independent simulations ---- */
 
 /* Group n simulations (created on the same device, any sizes and parameters,

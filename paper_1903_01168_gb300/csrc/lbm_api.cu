@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 
 using namespace lbm;
@@ -652,6 +653,20 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
 }
 
 }  // namespace
+
+namespace lbm {
+
+lbm_status host_validate(int nx, int ny, const lbm_params *p, char *err) { return validate(nx, ny, p, err); }
+
+void host_fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p, void *state) {
+    fill_desc(h, nx, ny, p);
+    h.rho = reinterpret_cast<float *>(state);
+    h.dev = static_cast<char *>(state) + rho_region_bytes(nx, ny);
+}
+
+void host_set_global_error(const char *msg) { snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
+
+}  // namespace lbm
 
 extern "C" {
 

@@ -707,6 +707,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag(const SimDesc *__restrict
     block_reduce_store(acc, part);
 }
 
+#ifndef LBM_DEVICE_HELPERS_ONLY   // non-template kernels: defined in one translation unit
 // Sum the per-block partials in block order (deterministic) into out[DIAG_NQ].
 __global__ void k_diag_final(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
     const int q = threadIdx.x;
@@ -727,5 +728,7 @@ __global__ void k_advance(SimDesc *descs, int n, long long k) {
 __global__ void k_set_t0(SimDesc *desc, long long t) {
     if (threadIdx.x == 0 && blockIdx.x == 0) desc->t0 = t;
 }
+
+#endif
 
 }  // namespace lbm

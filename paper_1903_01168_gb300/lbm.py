@@ -37,6 +37,7 @@ ABI_SYMBOLS = (
     "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
     "lbm_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_last_error",
     "lbm_destroy", "lbm_batch_create", "lbm_batch_step", "lbm_batch_items", "lbm_batch_destroy",
+    "lbm_step_noalloc",
 )
 
 
@@ -122,6 +123,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
+    L.lbm_step_noalloc.argtypes = [pp, i, i, vp, st, ctypes.c_longlong, l, vp]
     L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
     L.lbm_batch_step.argtypes = [vp, l, i]
     L.lbm_batch_items.argtypes = [vp]
@@ -242,6 +244,14 @@ def lbm_last_error(sim) -> str:
 def lbm_destroy(sim: int):
     if sim:
         load().lbm_destroy(sim)
+
+
+def lbm_step_noalloc(p: lbm_params, nx: int, ny: int, state_ptr: int, nbytes: int, t: int, n: int,
+                     stream: int = 0):
+    """Advance a caller-owned device state buffer by n steps without any device
+    allocation (see include/lbm.h)."""
+    _check(load().lbm_step_noalloc(ctypes.byref(p), nx, ny, ctypes.c_void_p(state_ptr), nbytes, int(t), int(n),
+                                   ctypes.c_void_p(stream)))
 
 
 def lbm_batch_create(sims, rows_per_item: int = 0) -> int:
