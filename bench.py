@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic of one k_step_fused launch on this workload from an ncu capture
 # (profiles/k_step_fused_laplace_sweep_256.md), valid only for the kernel
 # sources with this hash; reported as null otherwise.
-NCU_TRAFFIC = {"sources_sha": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"sources_sha": "78947a3b6ff155d5", "bytes_per_launch": 258693120 + 163757568}
 
 
 def kernel_sources_sha() -> str:
