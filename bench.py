@@ -30,11 +30,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_UPDATE = {0: 144, 1: 72, 2: 72}   # 18 populations read + written
+# per node update: 2 FP32 densities + 16 deviations, read and written
+BYTES_PER_UPDATE = {0: 144, 1: 80, 2: 80}
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic of one k_step_fused launch on this workload from an ncu capture
-# (profiles/k_step_fused_laplace_sweep_256.md), valid only for the kernel
+# (profiles/k_step_fused_laplace_sweep_40x256.md), valid only for the kernel
 # sources with this hash; reported as null otherwise.
 NCU_TRAFFIC = {"sources_sha": "78947a3b6ff155d5", "bytes_per_launch": 258693120 + 163757568}
 
@@ -186,6 +187,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage: FP32, or FP16 / BF16 deviations (FP32 arithmetic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -207,17 +210,17 @@ def main():
     L.load(build_if_missing=(rank == 0 and world == 1))
 
     specs = workload()
+    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
     stream = torch.cuda.Stream()
     sims = []
     with torch.cuda.stream(stream):
         for sp in specs:
             s = L.Simulation(sp.nx, sp.ny, torch_memory=True, gamma=sp.gamma, tau_r=sp.tau_r,
-                             tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta)
+                             tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta, storage=storage)
             s.init_bubble(*sp.bubble)
             sims.append(s)
         batch = L.Batch(sims)
     nodes = sum(sp.nx * sp.ny for sp in specs)
-    storage = 0
 
     def barrier():
         if dist is not None:
@@ -268,6 +271,7 @@ def main():
         tt = torch.tensor([te], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         te = float(tt.item())
+    algo_bytes = BYTES_PER_UPDATE[storage] * nodes
     h2d = sum(4 * sp.nx * sp.ny * 8 for sp in specs)
     d2h = sum(5 * sp.nx * sp.ny * 8 for sp in specs)
     e2e = {"value": nodes * args.steps * world / te / 1e6, "unit": "MLUPS",
@@ -276,17 +280,18 @@ def main():
     assert all(np.isfinite(o["rho_r"]).all() for o in outs)
 
     peak, peak_kind = measured_peak()
-    algo_bytes = BYTES_PER_UPDATE[storage] * nodes
     achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sources_sha"] == kernel_sources_sha() else None
+    traffic = (NCU_TRAFFIC["bytes_per_launch"]
+               if NCU_TRAFFIC["sources_sha"] == kernel_sources_sha() and storage == 0 else None)
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "laplace_sweep_40x256x256_f32", "lattices": 40, "nx": 256, "ny": 256,
-                   "nodes_per_step": nodes, "storage": "f32", "kernel": "k_step_fused (batched, graph)",
+        "config": {"workload": f"laplace_sweep_40x256x256_{args.storage}", "lattices": 40, "nx": 256, "ny": 256,
+                   "nodes_per_step": nodes, "storage": args.storage, "kernel": "k_step_fused (batched, graph)",
                    "work_items": batch.items,
-                   "l2": "inputs larger than L2: 2 x 189 MB of populations per step", "parallelism":
+                   "l2": f"inputs larger than L2: {2 * algo_bytes / 2e6:.0f} MB of state touched per step",
+                   "parallelism":
                    "replicas only" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
