@@ -125,6 +125,38 @@ def workload():
     return W.laplace_sweep(256, steps=20000)
 
 
+def ensemble_workload():
+    from paper_1903_01168_gb300 import workloads as W
+    return W.ensemble(seed=W.DEFAULT_SEED, n_sims=256)
+
+
+def run_serving(args):
+    """Serving trace: Poisson arrivals of open-channel slug requests (mixed lattice
+    sizes, step counts and storage types) through the continuous-batching server,
+    then the same trace one request at a time through the plain FP32 path."""
+    import torch
+    from paper_1903_01168_gb300 import lbm as L
+    from paper_1903_01168_gb300 import serving as S
+    from paper_1903_01168_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    L.load(build_if_missing=True)
+    trace = W.serving_trace(seed=W.DEFAULT_SEED, n_requests=args.requests, rate_hz=args.rate)
+    # warm up kernels and graphs of every storage type
+    warm = [(0.0, W.SimSpec(**{**sp.as_dict(), "nx": 256, "ny": 64, "steps": 64})) for _, sp in trace[:3]]
+    S.Server(budget_bytes=150e9, chunk=32).run(warm)
+    S.run_sequential(warm)
+    res_b, st_b = S.Server(budget_bytes=150e9, chunk=args.chunk).run(trace)
+    res_s, st_s = S.run_sequential(trace, storage=0)
+    line = {"metric": "MLUPS", "value": st_b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving_{args.requests}_requests_poisson_{args.rate}hz",
+                       "budget_bytes": 150e9, "chunk_steps": args.chunk},
+            "serving": {k: st_b[k] for k in ("requests", "p50_s", "p99_s", "mean_s", "makespan_s", "mlups")},
+            "sequential_f32": {k: st_s[k] for k in ("requests", "p50_s", "p99_s", "mean_s", "makespan_s",
+                                                     "mlups")}}
+    print(json.dumps(line), flush=True)
+
+
 def oracle_mlups(specs, steps: int, seconds: float):
     """FP64 oracle on a bounded sample: one sweep run at a time, `steps` steps each,
     until `seconds` of CPU work have been spent.  Returns (MLUPS, sample text)."""
@@ -187,15 +219,26 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="laplace_sweep", choices=["laplace_sweep", "ensemble", "serving"],
+                    help="laplace_sweep: 40 x 256^2 (default); ensemble: 256 uneven lattices, FP16 "
+                         "deviations; serving: Poisson-arrival open-channel requests")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage: FP32, or FP16 / BF16 deviations (FP32 arithmetic)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the measured choice of plan_rows per size class (default plan)")
+    ap.add_argument("--requests", type=int, default=24, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=1.5, help="serving: Poisson arrival rate (1/s)")
+    ap.add_argument("--chunk", type=int, default=500, help="serving: steps per batched chunk")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
 
     import numpy as np
@@ -209,15 +252,30 @@ def main():
     torch.cuda.set_device(local)
     L.load(build_if_missing=(rank == 0 and world == 1))
 
-    specs = workload()
+    specs = workload() if args.workload == "laplace_sweep" else ensemble_workload()
     storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    if args.workload == "ensemble":
+        storage = 1   # the ensemble is defined with FP16-deviation storage
     stream = torch.cuda.Stream()
+    sim_params = [dict(gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta,
+                       storage=storage, gx=sp.gx, bc_y=sp.bc_y) for sp in specs]
+    tuned = None
+    if not args.no_autotune:
+        from paper_1903_01168_gb300.autotune import Autotuner
+        tuner = Autotuner()
+        ta = time.perf_counter()
+        with torch.cuda.stream(stream):
+            tuned = tuner.tune_batch([(sp.nx, sp.ny, kw) for sp, kw in zip(specs, sim_params)])
+        tune_s = time.perf_counter() - ta
+        sim_params = [tuner.params_for(sp.nx, sp.ny, True, **kw) for sp, kw in zip(specs, sim_params)]
     sims = []
     with torch.cuda.stream(stream):
-        for sp in specs:
-            s = L.Simulation(sp.nx, sp.ny, torch_memory=True, gamma=sp.gamma, tau_r=sp.tau_r,
-                             tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta, storage=storage)
-            s.init_bubble(*sp.bubble)
+        for sp, kw in zip(specs, sim_params):
+            s = L.Simulation(sp.nx, sp.ny, torch_memory=True, **kw)
+            if sp.geometry == "bubble":
+                s.init_bubble(*sp.bubble)
+            else:
+                s.init_slug(int(sp.slug[0]), sp.slug[1], sp.slug[2], True)
             sims.append(s)
         batch = L.Batch(sims)
     nodes = sum(sp.nx * sp.ny for sp in specs)
@@ -256,7 +314,12 @@ def main():
     host_fields = []
     from paper_1903_01168_gb300 import workloads as W
     for sp in specs:
-        host_fields.append([np.ascontiguousarray(a) for a in W.bubble_fields(sp.nx, sp.ny, *sp.bubble, sp.gamma)])
+        if sp.geometry == "bubble":
+            f = W.bubble_fields(sp.nx, sp.ny, *sp.bubble, sp.gamma)
+        else:
+            f = W.slug_fields(sp.nx, sp.ny, sp.gamma, int(sp.slug[0]), sp.slug[1], sp.slug[2], g=sp.gx,
+                              nu_l=sp.extra.get("nu_l", 0.1))
+        host_fields.append([np.ascontiguousarray(a) for a in f])
     barrier()
     torch.cuda.synchronize()
     te0 = time.perf_counter()
@@ -287,9 +350,16 @@ def main():
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"laplace_sweep_40x256x256_{args.storage}", "lattices": 40, "nx": 256, "ny": 256,
-                   "nodes_per_step": nodes, "storage": args.storage, "kernel": "k_step_fused (batched, graph)",
+        "config": {"workload": (f"laplace_sweep_40x256x256_{args.storage}" if args.workload == "laplace_sweep"
+                                else "ensemble_256_uneven_f16dev"),
+                   "lattices": len(specs), "nx": specs[0].nx if args.workload == "laplace_sweep" else "64..512",
+                   "ny": specs[0].ny if args.workload == "laplace_sweep" else "64..1024",
+                   "nodes_per_step": nodes, "storage": ["f32", "f16", "bf16"][storage],
+                   "kernel": "k_step_fused (batched, graph)",
                    "work_items": batch.items,
+                   "autotune": (None if tuned is None else
+                                {"seconds": round(tune_s, 2),
+                                 "plan_rows": {k.removeprefix("batch-"): v["plan_rows"] for k, v in tuned.items()}}),
                    "l2": f"inputs larger than L2: {2 * algo_bytes / 2e6:.0f} MB of state touched per step",
                    "parallelism":
                    "replicas only" if world > 1 else "single GPU"},
@@ -300,7 +370,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": args.steps + 1,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "laplace_sweep":
         v, sample = oracle_mlups(specs, 100, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:

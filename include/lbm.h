@@ -89,6 +89,11 @@ typedef struct {
     int inlet_period_r, inlet_period_b; /* ALTERNATE: steps of red, then blue injection */
     int inlet_layer;     /* LAYERED: rows y < inlet_layer inject red, the rest blue */
     int kernel;          /* lbm_kernel */
+    int plan_rows;       /* fused kernel work plan: fewest rows of this lattice a thread
+                            block marches over in one segment (0 = 8), alone or in a
+                            batch; larger values trade parallelism for less halo
+                            re-reading.  Never changes results, only speed (the
+                            Python autotuner picks it per lattice size class). */
 } lbm_params;
 
 /* FP64 diagnostics of the state at the current time t (sums over all nodes). */
@@ -156,6 +161,12 @@ lbm_status lbm_init_populations(lbm_sim *s, const double *pops);
 /* Advance n >= 0 time steps (asynchronous on the simulation's stream). */
 lbm_status lbm_step(lbm_sim *s, long n);
 
+/* Stop the simulation at time t_end (t_end >= current time; t_end < 0 removes
+ * the stop): steps that would start at t >= t_end leave the state unchanged, so
+ * lbm_step / lbm_batch_step may run past it and the state stays at t_end.
+ * Batches created before the call keep the previous stop time.  Synchronous. */
+lbm_status lbm_set_stop(lbm_sim *s, long long t_end);
+
 /* Block until the simulation's queued work is done; reports CUDA errors. */
 lbm_status lbm_synchronize(lbm_sim *s);
 
@@ -221,10 +232,12 @@ lbm_status lbm_step_noalloc(const lbm_params *p, int nx, int ny, void *state, si
 
 /* Group n simulations (created on the same device, any sizes and parameters,
  * FP32 or 16-bit storage) so that lbm_batch_step advances all of them with one
- * kernel launch per time step on the stream of sims[0].  rows_per_item > 0
- * fixes the number of lattice rows each thread block marches over; 0 picks it
- * from the built-in size-class table.  The simulations stay owned by the
- * caller and must outlive the batch. */
+ * kernel launch per time step and storage / collision type (types run
+ * concurrently on streams of the batch, joined into the stream of sims[0]).
+ * rows_per_item > 0 cuts every strip into pieces of that many rows, one per
+ * thread block; 0 spreads the rows of all members evenly over the resident
+ * thread blocks, no segment of a member shorter than its plan_rows.
+ * The simulations stay owned by the caller and must outlive the batch. */
 lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out);
 
 /* Advance every simulation of the batch by n steps; with use_graph != 0 the

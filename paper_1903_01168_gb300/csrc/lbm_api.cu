@@ -99,6 +99,7 @@ struct lbm_sim {
 struct lbm_batch {
     std::vector<lbm_sim *> sims;
     std::vector<long long> t_mirror;  // t0 of each batch descriptor as last written
+    std::vector<long long> t_stop;    // stop time baked into each batch descriptor
     SimDesc *d_descs = nullptr;
     WorkItem *d_items = nullptr;
     int *d_off = nullptr;
@@ -107,6 +108,10 @@ struct lbm_batch {
     // ranges off[off0 .. off0 + blocks]
     struct Group { int storage, variant, item0, off0, blocks; };
     std::vector<Group> groups;
+    // groups beyond the first run concurrently on their own streams (fork / join)
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gjoin;
+    cudaEvent_t fork = nullptr;
     int *d_err = nullptr;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -153,6 +158,7 @@ lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
     }
     if (p->storage < 0 || p->storage > 2) { set_err(err, "unknown storage"); return LBM_EINVAL; }
     if (p->kernel < 0 || p->kernel > 2) { set_err(err, "unknown kernel"); return LBM_EINVAL; }
+    if (p->plan_rows < 0 || p->plan_rows > (1 << 20)) { set_err(err, "plan_rows out of range"); return LBM_EINVAL; }
     if (p->bc_x == LBM_BC_INOUT && !(p->p_out > 0.0)) {
         set_err(err, "inlet/outlet needs p_out > 0");
         return LBM_EINVAL;
@@ -179,8 +185,11 @@ size_t dev_region_bytes(int nx, int ny, int storage) {
 }
 
 // Per-simulation constants of Sec. 2.1 in the descriptor (float).
+constexpr long long NO_STOP = 1LL << 62;
+
 void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     memset(&h, 0, sizeof(h));
+    h.t_end = NO_STOP;
     h.storage = p->storage;
     h.variant = variant_of(p);
     h.ghost = GHOST;
@@ -272,6 +281,7 @@ lbm_status encode_tmap(lbm_sim *s) {
 
 struct StripRef {
     int sim, x0, w, ny;
+    int min_piece;   // shortest row range of this strip worth its 4-row halo
 };
 
 struct Plan {
@@ -280,39 +290,45 @@ struct Plan {
     int blocks = 0;
 };
 
-void strips_of(std::vector<StripRef> &out, int sim, int nx, int ny) {
-    for (int x0 = 0; x0 < nx; x0 += FUSED_W) out.push_back({sim, x0, std::min(FUSED_W, nx - x0), ny});
+constexpr int MIN_PIECE = 8;   // default shortest row range worth a 4-row halo
+
+void strips_of(std::vector<StripRef> &out, int sim, int nx, int ny, int plan_rows) {
+    const int mp = plan_rows > 0 ? plan_rows : MIN_PIECE;
+    for (int x0 = 0; x0 < nx; x0 += FUSED_W) out.push_back({sim, x0, std::min(FUSED_W, nx - x0), ny, mp});
 }
 
-constexpr int MIN_PIECE = 8;   // shortest row range worth a 4-row halo
-
 // Balanced persistent plan: the strip rows (weighted by the warps a strip
-// keeps busy) are cut into max_blocks nearly equal shares, in order, so a block
-// may march over the end of one strip and the start of the next.
+// keeps busy) are cut into nearly equal shares, in order, so a block may march
+// over the end of one strip and the start of the next.  The share count is
+// max_blocks, or fewer when the strips' own shortest pieces would not fill them.
 Plan balanced_plan(const std::vector<StripRef> &strips, int max_blocks) {
     Plan P;
-    double total = 0.0;
-    for (const auto &s : strips) total += (double)s.ny * ((s.w + 31) / 32);
-    const double full_rows = total / 4.0;
-    int B = (int)std::min<double>(max_blocks, std::max(1.0, std::floor(full_rows / MIN_PIECE)));
+    double total = 0.0, pieces = 0.0;
+    for (const auto &s : strips) {
+        const int wc = (s.w + 31) / 32;
+        total += (double)s.ny * wc;
+        pieces += (double)s.ny * wc / 4.0 / std::max(1, s.min_piece);
+    }
+    int B = (int)std::min<double>(max_blocks, std::max(1.0, std::floor(pieces)));
     const double quota = total / B;
     P.off.push_back(0);
     int b = 0;
     double acc = 0.0;
     for (const auto &s : strips) {
         const int wc = (s.w + 31) / 32;
+        const int mp = std::max(1, s.min_piece);
         int y = 0;
         while (y < s.ny) {
             const double left = quota * (b + 1) - acc;
             int take = (int)std::floor(left / wc + 1e-9);
-            if (take < MIN_PIECE && b < B - 1 && (int)P.items.size() > P.off.back()) {
+            if (take < mp && b < B - 1 && (int)P.items.size() > P.off.back()) {
                 P.off.push_back((int)P.items.size());   // close block b, continue in b + 1
                 ++b;
                 continue;
             }
-            take = std::max(take, MIN_PIECE);
+            take = std::max(take, mp);
             take = std::min(take, s.ny - y);
-            if (s.ny - (y + take) < MIN_PIECE) take = s.ny - y;   // no tiny tail pieces
+            if (s.ny - (y + take) < mp) take = s.ny - y;   // no tiny tail pieces
             WorkItem it{};
             it.sim = s.sim;
             it.x0 = s.x0;
@@ -617,7 +633,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
     }
     {
         std::vector<StripRef> strips;
-        strips_of(strips, 0, nx, ny);
+        strips_of(strips, 0, nx, ny, p->plan_rows);
         Plan P = balanced_plan(strips, resident_blocks(p->storage));
         s->n_items = (int)P.items.size();
         s->n_blocks = P.blocks;
@@ -793,8 +809,20 @@ lbm_status lbm_step(lbm_sim *s, long n) {
         st = step_direct(s, n - done);
         if (st != LBM_OK) return st;
     }
-    s->t += n;
-    s->dev_t0 = s->t;
+    const long long t_old = s->t;
+    s->t = std::min(t_old + n, s->h.t_end);   // steps at or after the stop time were skipped
+    s->dev_t0 = t_old + n;                    // what the device descriptor now holds
+    return LBM_OK;
+}
+
+lbm_status lbm_set_stop(lbm_sim *s, long long t_end) {
+    if (!s) return LBM_EINVAL;
+    const long long te = t_end < 0 ? NO_STOP : t_end;
+    if (te < s->t) { set_err(s->err, "stop time %lld is before the current time %lld", te, s->t); return LBM_EINVAL; }
+    s->h.t_end = te;
+    CK(cudaMemcpyAsync(&s->d_desc->t_end, &s->h.t_end, sizeof(long long), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->dev_t0 = -1;
     return LBM_OK;
 }
 
@@ -946,6 +974,7 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
         descs[i] = sims[i]->h;
         descs[i].t0 = sims[i]->t;
         b->t_mirror.push_back(sims[i]->t);
+        b->t_stop.push_back(sims[i]->h.t_end);
     }
     // items grouped by (storage, variant): one launch per group and step
     std::vector<int> offs;
@@ -953,9 +982,11 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
         for (int cv = 0; cv < 4; cv++) {
             std::vector<StripRef> strips;
             for (int i = 0; i < n; i++)
-                if (sims[i]->p.storage == st && sims[i]->h.variant == cv) strips_of(strips, i, sims[i]->nx, sims[i]->ny);
+                if (sims[i]->p.storage == st && sims[i]->h.variant == cv)
+                    strips_of(strips, i, sims[i]->nx, sims[i]->ny, sims[i]->p.plan_rows);
             if (strips.empty()) continue;
-            Plan P = rows_per_item > 0 ? fixed_plan(strips, rows_per_item) : balanced_plan(strips, resident_blocks(st));
+            Plan P = rows_per_item > 0 ? fixed_plan(strips, rows_per_item)
+                                       : balanced_plan(strips, resident_blocks(st));
             lbm_batch::Group g{st, cv, (int)items.size(), (int)offs.size(), P.blocks};
             for (int &o : P.off) o += g.item0;
             items.insert(items.end(), P.items.begin(), P.items.end());
@@ -975,6 +1006,23 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
         lbm_batch_destroy(b);
         return LBM_ENOMEM;
     }
+    for (size_t g = 1; g < b->groups.size(); g++) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            set_err(g_create_err, "batch stream creation failed");
+            lbm_batch_destroy(b);
+            return LBM_ECUDA;
+        }
+        b->gstreams.push_back(st);
+        b->gjoin.push_back(ev);
+    }
+    if (b->groups.size() > 1 && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        set_err(g_create_err, "batch event creation failed");
+        lbm_batch_destroy(b);
+        return LBM_ECUDA;
+    }
     // work queued on member streams must be complete before the batch runs on sims[0]'s stream
     for (int i = 0; i < n; i++) cudaStreamSynchronize(sims[i]->stream);
     *out = b;
@@ -988,20 +1036,33 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
     lbm_sim *s = b->sims[0];
     if (n < 0) { set_err(s->err, "n < 0"); return LBM_EINVAL; }
     if (n == 0) return LBM_OK;
-    // resynchronise descriptors of members stepped outside the batch
+    // resynchronise descriptors of members stepped outside the batch (their
+    // logical time no longer matches the batch descriptor's t0, clamped at the stop)
     for (size_t i = 0; i < b->sims.size(); i++) {
-        if (b->t_mirror[i] != b->sims[i]->t) {
-            k_set_t0<<<1, 32, 0, b->stream>>>(b->d_descs + i, b->sims[i]->t);
+        lbm_sim *m = b->sims[i];
+        if (std::min(b->t_mirror[i], m->h.t_end) != m->t || b->t_stop[i] != m->h.t_end) {
+            k_set_t0<<<1, 32, 0, b->stream>>>(b->d_descs + i, m->t);
             CK(cudaGetLastError());
-            b->t_mirror[i] = b->sims[i]->t;
+            b->t_mirror[i] = m->t;
         }
     }
     const int nsims = (int)b->sims.size();
+    // Groups are independent simulations: each runs its k steps on its own stream,
+    // forked from and joined back into the batch stream.
     auto run = [&](long k) -> lbm_status {
-        for (long j = 0; j < k; j++)
-            for (const auto &g : b->groups)
+        if (b->groups.size() > 1) CK(cudaEventRecord(b->fork, b->stream));
+        for (size_t gi = 0; gi < b->groups.size(); gi++) {
+            const auto &g = b->groups[gi];
+            cudaStream_t st = gi == 0 ? b->stream : b->gstreams[gi - 1];
+            if (gi > 0) CK(cudaStreamWaitEvent(st, b->fork, 0));
+            for (long j = 0; j < k; j++)
                 CK(launch_fused_any(g.storage, g.variant, b->d_descs, b->d_items, b->d_off + g.off0, g.blocks, (int)j,
-                                    b->d_err, b->stream));
+                                    b->d_err, st));
+            if (gi > 0) {
+                CK(cudaEventRecord(b->gjoin[gi - 1], st));
+                CK(cudaStreamWaitEvent(b->stream, b->gjoin[gi - 1], 0));
+            }
+        }
         k_advance<<<(nsims + 127) / 128, 128, 0, b->stream>>>(b->d_descs, nsims, k);
         CK(cudaGetLastError());
         return LBM_OK;
@@ -1026,8 +1087,11 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
         if (st != LBM_OK) return st;
     }
     for (size_t i = 0; i < b->sims.size(); i++) {
-        b->sims[i]->t += n;
-        b->t_mirror[i] = b->sims[i]->t;
+        lbm_sim *m = b->sims[i];
+        const long long tb = b->t_mirror[i] + n;             // batch descriptor's t0 now
+        m->t = std::min(m->t + n, m->h.t_end);
+        b->t_mirror[i] = tb;
+        b->t_stop[i] = m->h.t_end;
     }
     // members' own streams must see the batch's work before their next call
     cudaEvent_t ev;
@@ -1043,6 +1107,12 @@ void lbm_batch_destroy(lbm_batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto st : b->gstreams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (auto ev : b->gjoin) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->d_descs);
     cudaFree(b->d_items);
     cudaFree(b->d_off);

@@ -63,6 +63,7 @@ struct alignas(128) SimDesc {
     long long rho_plane, rho_buf;   // element strides
     long long dev_plane, dev_buf;
     long long t0;              // time of the state when a launch chunk starts
+    long long t_end;           // steps that would start at t >= t_end are skipped
     int pitch_r, pitch_d, ghost;
     int storage, variant;      // variant: bit 0 MRT, bit 1 Hermite equilibrium
     Phys ph;
@@ -159,27 +160,26 @@ struct NodeStore {
 // inlet alternates red / blue segments in time, or is layered in y.
 __device__ __forceinline__ float inlet_red_fraction(const Phys &p, int y, long long t) {
     if (p.inlet_mode == 1) return y < p.inlet_layer ? 1.0f : 0.0f;
-    long long period = (long long)p.inlet_period_r + p.inlet_period_b;
+    const int period = p.inlet_period_r + p.inlet_period_b;
     if (period <= 0) return 1.0f;
-    return (t % period) < p.inlet_period_r ? 1.0f : 0.0f;
+    return (int)(t % period) < p.inlet_period_r ? 1.0f : 0.0f;
 }
 
 // Two-phase Zou-He velocity inlet on the west column (Sec. 2.5, the north inlet
 // rotated by +90 degrees): unknowns 1, 5, 8, colour split by the injected phase.
-// Evaluated in FP64: the mass balance divides by (1 - v) and the outlet below
-// subtracts 1 from a ratio near 1, which FP32 resolves only to ~1e-7.
-__device__ __forceinline__ void zouhe_inlet(const Phys &p, bool hermite, double f_r, double (&nr)[9],
-                                            double (&nb)[9]) {
-    double n[9];
+// R is the arithmetic type (FP32 on the step path, FP64 for state export).
+template <typename R>
+__device__ __forceinline__ void zouhe_inlet(const Phys &p, bool hermite, R f_r, R (&nr)[9], R (&nb)[9]) {
+    R n[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) n[i] = nr[i] + nb[i];
-    const double f_b = 1.0 - f_r;
-    const double Vx = f_r * p.u_in_r + f_b * p.u_in_b;
-    const double rho = (n[0] + n[2] + n[4] + 2.0 * (n[3] + n[6] + n[7])) / (1.0 - Vx);
-    const double H = hermite ? -rho * (f_r * p.herm_r + f_b * p.herm_b) * Vx / 3.0 : 0.0;
-    const double n1 = n[3] + (2.0 / 3.0) * rho * Vx + H;
-    const double n5 = n[7] + 0.5 * (n[4] - n[2]) + rho * Vx / 6.0 - 0.5 * H;
-    const double n8 = n[6] + 0.5 * (n[2] - n[4]) + rho * Vx / 6.0 - 0.5 * H;
+    const R f_b = R(1) - f_r;
+    const R Vx = f_r * R(p.u_in_r) + f_b * R(p.u_in_b);
+    const R rho = (n[0] + n[2] + n[4] + R(2) * (n[3] + n[6] + n[7])) / (R(1) - Vx);
+    const R H = hermite ? -rho * (f_r * R(p.herm_r) + f_b * R(p.herm_b)) * Vx / R(3) : R(0);
+    const R n1 = n[3] + (R(2) / R(3)) * rho * Vx + H;
+    const R n5 = n[7] + R(0.5) * (n[4] - n[2]) + rho * Vx / R(6) - R(0.5) * H;
+    const R n8 = n[6] + R(0.5) * (n[2] - n[4]) + rho * Vx / R(6) - R(0.5) * H;
     nr[1] = f_r * n1; nb[1] = f_b * n1;
     nr[5] = f_r * n5; nb[5] = f_b * n5;
     nr[8] = f_r * n8; nb[8] = f_b * n8;
@@ -188,21 +188,24 @@ __device__ __forceinline__ void zouhe_inlet(const Phys &p, bool hermite, double 
 // Two-phase Zou-He pressure outlet on the east column (the south outlet rotated
 // by +90 degrees): unknowns 3, 6, 7; colour fraction from the known populations,
 // rho_out = f_b p_out / (c_s^b)^2 + f_r p_out / (c_s^r)^2, v = -1 + (...)/rho_out.
-__device__ __forceinline__ void zouhe_outlet(const Phys &p, bool hermite, double (&nr)[9], double (&nb)[9]) {
-    const double kr = nr[0] + nr[1] + nr[2] + nr[4] + nr[5] + nr[8];
-    const double kb = nb[0] + nb[1] + nb[2] + nb[4] + nb[5] + nb[8];
-    const double a = kr * (double)p.inv_gamma;
-    const double psi = (a - kb) / (a + kb);
-    const double f_r = 0.5 * (1.0 + psi), f_b = 1.0 - f_r;
-    double n[9];
+template <typename R>
+__device__ __forceinline__ void zouhe_outlet(const Phys &p, bool hermite, R (&nr)[9], R (&nb)[9]) {
+    const R kr = nr[0] + nr[1] + nr[2] + nr[4] + nr[5] + nr[8];
+    const R kb = nb[0] + nb[1] + nb[2] + nb[4] + nb[5] + nb[8];
+    const R a = kr * R(p.inv_gamma);
+    const R psi = (a - kb) / (a + kb);
+    const R f_r = R(0.5) * (R(1) + psi), f_b = R(1) - f_r;
+    R n[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) n[i] = nr[i] + nb[i];
-    const double rho = f_b * p.p_out / p.cs2_b + f_r * p.p_out / p.cs2_r;
-    const double Vx = -1.0 + (n[0] + n[2] + n[4] + 2.0 * (n[1] + n[5] + n[8])) / rho;
-    const double H = hermite ? rho * (f_r * p.herm_r + f_b * p.herm_b) * Vx / 3.0 : 0.0;
-    const double n3 = n[1] - (2.0 / 3.0) * rho * Vx + H;
-    const double n6 = n[8] - 0.5 * (n[2] - n[4]) - rho * Vx / 6.0 - 0.5 * H;
-    const double n7 = n[5] + 0.5 * (n[2] - n[4]) - rho * Vx / 6.0 - 0.5 * H;
+    const R rho = f_b * R(p.p_out) / R(p.cs2_b) + f_r * R(p.p_out) / R(p.cs2_r);
+    // v = -1 + S / rho written as (S - rho) / rho
+    const R S = n[0] + n[2] + n[4] + R(2) * (n[1] + n[5] + n[8]);
+    const R Vx = (S - rho) / rho;
+    const R H = hermite ? rho * (f_r * R(p.herm_r) + f_b * R(p.herm_b)) * Vx / R(3) : R(0);
+    const R n3 = n[1] - (R(2) / R(3)) * rho * Vx + H;
+    const R n6 = n[8] - R(0.5) * (n[2] - n[4]) - rho * Vx / R(6) - R(0.5) * H;
+    const R n7 = n[5] + R(0.5) * (n[2] - n[4]) - rho * Vx / R(6) - R(0.5) * H;
     nr[3] = f_r * n3; nb[3] = f_b * n3;
     nr[6] = f_r * n6; nb[6] = f_b * n6;
     nr[7] = f_r * n7; nb[7] = f_b * n7;
@@ -273,34 +276,30 @@ __device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x
         P.e[0] = -e0;
         return;
     }
-    // open column: full populations, Zou-He, then moments (FP64, two columns only)
-    double nr[9], nb[9];
+    // open column: full populations, Zou-He, then moments
+    float nr[9], nb[9];
     {
-        double sr = 0.0, sb = 0.0;
+        float sr = 0.0f, sb = 0.0f;
 #pragma unroll
         for (int i = 1; i < 9; i++) {
-            nr[i] = (double)p.phi_r[C2(i)] * s[0][i] + dl[0][i];
-            nb[i] = (double)p.phi_b[C2(i)] * s[1][i] + dl[1][i];
+            nr[i] = p.phi_r[C2(i)] * s[0][i] + dl[0][i];
+            nb[i] = p.phi_b[C2(i)] * s[1][i] + dl[1][i];
             sr += ld.dev(0, i, x, y);
             sb += ld.dev(1, i, x, y);
         }
-        nr[0] = (double)p.phi_r[0] * own_rho[0] - sr;
-        nb[0] = (double)p.phi_b[0] * own_rho[1] - sb;
+        nr[0] = p.phi_r[0] * own_rho[0] - sr;
+        nb[0] = p.phi_b[0] * own_rho[1] - sb;
     }
     const int yw = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
-    if (x == 0) zouhe_inlet(p, HERMITE, inlet_red_fraction(p, yw, t), nr, nb);
-    else zouhe_outlet(p, HERMITE, nr, nb);
-    double rr = 0.0, rb = 0.0;
+    if (x == 0) zouhe_inlet<float>(p, HERMITE, inlet_red_fraction(p, yw, t), nr, nb);
+    else zouhe_outlet<float>(p, HERMITE, nr, nb);
+    float rr = 0.0f, rb = 0.0f;
 #pragma unroll
     for (int i = 0; i < 9; i++) { rr += nr[i]; rb += nb[i]; }
-    P.rr = (float)rr;
-    P.rb = (float)rb;
-    // non-rest parts relative to the densities as they will be stored (FP32),
-    // so that the stored state reproduces the node's populations
-    const double rrf = P.rr, rbf = P.rb;
+    P.rr = rr;
+    P.rb = rb;
 #pragma unroll
-    for (int i = 0; i < 9; i++)
-        P.e[i] = (float)((nr[i] + nb[i]) - (rrf * (double)p.phi_r[C2(i)] + rbf * (double)p.phi_b[C2(i)]));
+    for (int i = 0; i < 9; i++) P.e[i] = (nr[i] + nb[i]) - (rr * p.phi_r[C2(i)] + rb * p.phi_b[C2(i)]);
 }
 
 // Moments of the pulled node (x, y) without forming its populations: the new
@@ -378,8 +377,8 @@ __device__ __forceinline__ void pull_populations(const Phys &p, const Loader &ld
     nr[0] = (double)p.phi_r[0] * ld.rho(0, x, y) - sr;
     nb[0] = (double)p.phi_b[0] * ld.rho(1, x, y) - sb;
     if (p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1)) {
-        if (x == 0) zouhe_inlet(p, HERMITE, inlet_red_fraction(p, y, t), nr, nb);
-        else zouhe_outlet(p, HERMITE, nr, nb);
+        if (x == 0) zouhe_inlet<double>(p, HERMITE, inlet_red_fraction(p, y, t), nr, nb);
+        else zouhe_outlet<double>(p, HERMITE, nr, nb);
     }
 }
 

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
 
         const Phys p = d.ph;   // per-simulation constants, in registers from here on
         const long long t = d.t0 + step_offset;
+        if (t >= d.t_end) continue;   // this simulation has stopped
         const int bsrc = (int)(t & 1), bdst = bsrc ^ 1;
         const int nx = p.nx, ny = p.ny;
         const bool wall_y = p.bc_y == BC_WALL;
@@ -326,8 +327,8 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
                 // last warp computes them 16 lanes per node, unless a boundary
                 // touches them (open column, wall row) or the node needs q u
                 const int Ye = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
-                const bool edge_plain = !HERMITE_SRC && p.bc_x == BC_PERIODIC &&
-                                        !(wall_y && (Ye == 0 || Ye == ny - 1));
+                const bool edge_plain = !HERMITE_SRC && !(wall_y && (Ye == 0 || Ye == ny - 1)) &&
+                                        (p.bc_x == BC_PERIODIC || (x0 - 1 >= 1 && x0 + w <= nx - 2));
                 if (edge_plain) {
                     if (tid >= W - 32) {
                         const int lane = tid & 31, e = lane >> 4;
@@ -438,6 +439,7 @@ __global__ void k_tp_moments(const SimDesc *__restrict__ dp, int step_offset, fl
     const SimDesc &d = *dp;
     const Phys p = d.ph;
     const long long t = d.t0 + step_offset;
+    if (t >= d.t_end) return;   // this simulation has stopped
     const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
     const GlobalLoader<T> L(d, (int)(t & 1));
@@ -487,6 +489,7 @@ __global__ void k_tp_collide(const SimDesc *__restrict__ dp, int step_offset, co
     const SimDesc &d = *dp;
     const Phys p = d.ph;
     const long long t = d.t0 + step_offset;
+    if (t >= d.t_end) return;   // this simulation has stopped
     const int nx = p.nx, ny = p.ny;
     const long long n = (long long)nx * ny;
     const int bsrc = (int)(t & 1);

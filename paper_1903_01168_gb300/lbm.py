@@ -34,7 +34,7 @@ _STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4:
 # The C functions every build exports (declared in include/lbm.h).
 ABI_SYMBOLS = (
     "lbm_default_params", "lbm_bytes_required", "lbm_create", "lbm_create_ex", "lbm_init_bubble",
-    "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
+    "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_set_stop", "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
     "lbm_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_last_error",
     "lbm_destroy", "lbm_batch_create", "lbm_batch_step", "lbm_batch_items", "lbm_batch_destroy",
     "lbm_step_noalloc",
@@ -53,7 +53,7 @@ class lbm_params(ctypes.Structure):
         ("u_in_r", ctypes.c_double), ("u_in_b", ctypes.c_double), ("p_out", ctypes.c_double),
         ("inlet_mode", ctypes.c_int), ("inlet_period_r", ctypes.c_int),
         ("inlet_period_b", ctypes.c_int), ("inlet_layer", ctypes.c_int),
-        ("kernel", ctypes.c_int),
+        ("kernel", ctypes.c_int), ("plan_rows", ctypes.c_int),
     ]
 
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbm_init_fields.argtypes = [vp, dp, dp, dp, dp]
     L.lbm_init_populations.argtypes = [vp, dp]
     L.lbm_step.argtypes = [vp, l]
+    L.lbm_set_stop.argtypes = [vp, ctypes.c_longlong]
     L.lbm_synchronize.argtypes = [vp]
     L.lbm_time.argtypes = [vp]
     L.lbm_time.restype = ctypes.c_longlong
@@ -189,6 +190,10 @@ def lbm_init_populations(sim: int, pops):
 
 def lbm_step(sim: int, n: int):
     _check(load().lbm_step(sim, int(n)), sim)
+
+
+def lbm_set_stop(sim: int, t_end: int):
+    _check(load().lbm_set_stop(sim, int(t_end)), sim)
 
 
 def lbm_synchronize(sim: int):
@@ -343,6 +348,10 @@ class Simulation:
 
     def step(self, n: int = 1):
         lbm_step(self.h, n)
+
+    def set_stop(self, t_end: int):
+        """Steps at or after t_end leave the state unchanged (t_end < 0: no stop)."""
+        lbm_set_stop(self.h, t_end)
 
     def synchronize(self):
         lbm_synchronize(self.h)

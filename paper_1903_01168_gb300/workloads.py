@@ -214,7 +214,8 @@ def ensemble(seed: int = DEFAULT_SEED, n_sims: int = 256, steps: int = 10000) ->
                                beta=0.7, geometry="bubble", bubble=(nx / 2.0, ny / 2.0, R),
                                steps=steps, storage=1))
         else:
-            g = 1e-6
+            # body force for a centreline start speed of 0.01: g = 8 nu u_max / H^2, nu = 0.1
+            g = 8.0 * 0.1 * 0.01 / ny ** 2
             out.append(SimSpec(nx=nx, ny=ny, gamma=gamma, tau_r=0.8, tau_b=0.8, sigma=0.005,
                                beta=0.7, gx=g, bc_y=1, geometry="slug",
                                slug=(1, nx / 2.0, 0.5 * ny), steps=steps, storage=1,

@@ -189,6 +189,33 @@ def test_batch_equals_alone():
         s.close()
 
 
+def test_stop_times_in_a_batch():
+    """Members of one batch stopped at different times end exactly where the same
+    simulations stepped alone to those times end, bit for bit, and stay there."""
+    names = ["random_ragged_mrt_hermite", "walls_bgk_gravity", "tiny_8x4"]
+    stops = [13, 40, 27]
+    alone = []
+    for nm, te in zip(names, stops):
+        nx, ny, kw, make, _ = CASES[nm]
+        alone.append(_state_after(nx, ny, make(), te, **_gpu_params(kw)))
+    sims = []
+    for nm, te in zip(names, stops):
+        nx, ny, kw, make, _ = CASES[nm]
+        s = L.Simulation(nx, ny, **_gpu_params(kw))
+        s.init_fields(*make())
+        s.set_stop(te)
+        sims.append(s)
+    b = L.Batch(sims)
+    b.step(32, use_graph=True)
+    b.step(32, use_graph=True)
+    for s, te, ref in zip(sims, stops, alone):
+        assert s.t == te
+        assert s.save_state() == ref
+    b.close()
+    for s in sims:
+        s.close()
+
+
 def test_diagnostics_match_oracle_sums():
     nx, ny, kw, make, _ = CASES["walls_mrt_hermite"]
     f = make()
