@@ -240,6 +240,18 @@ lbm_status lbm_step_noalloc(const lbm_params *p, int nx, int ny, void *state, si
  * The simulations stay owned by the caller and must outlive the batch. */
 lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out);
 
+/* Work-plan options of a batch. */
+typedef struct {
+    int rows_per_item;   /* > 0: fixed plan, as in lbm_batch_create; 0: balanced plan */
+    float row_overhead;  /* balanced plan: cost of one strip row = the warps it keeps busy
+                            (1..4) + row_overhead; < 0 selects the library default (1).
+                            Changes only which block updates which rows, never results. */
+} lbm_batch_opts;
+
+/* lbm_batch_create with explicit plan options (opts must not be NULL).
+ * LBM_EINVAL for rows_per_item < 0 or row_overhead > 64. */
+lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts *opts, lbm_batch **out);
+
 /* Advance every simulation of the batch by n steps; with use_graph != 0 the
  * launches are captured once into a CUDA graph of n steps and replayed on
  * later calls with the same n. Asynchronous. */

@@ -13,7 +13,9 @@ wins.
 A size class is (storage type, collision, equilibrium, nx and ny rounded up to
 powers of two).  Tuning a single lattice times it alone; tuning for a batch
 times the members of each class together as a small batch, so the choice is the
-one that pays inside a batched launch.
+one that pays inside a batched launch.  A whole batch also gets its planner's
+row cost model tuned (`tune_row_overhead`): how much of a full strip row a
+narrow strip's row costs, which decides how many rows each block receives.
 
 The plan never changes what a node computes, so every candidate gives
 bit-identical results; only the time differs.
@@ -27,6 +29,7 @@ import os
 from . import lbm as L
 
 PLAN_CANDIDATES = (8, 16, 32, 64)
+ROW_OVERHEAD_CANDIDATES = (0.0, 0.5, 1.0, 2.0, 4.0)
 CLASS_SAMPLE = 4          # members of a class timed together when tuning a batch
 
 
@@ -151,3 +154,23 @@ class Autotuner:
             if not batched:
                 out["kernel"] = int(c["kernel"])
         return out
+
+
+def tune_row_overhead(sims, candidates=ROW_OVERHEAD_CANDIDATES, steps: int = 20) -> tuple[float, dict]:
+    """Planner cost of a strip row beyond its busy warps, timed on the batch itself.
+
+    The balanced plan shares the strip rows of all members among the resident
+    blocks by cost; how much a narrow strip's row costs relative to a full one
+    depends on the mix of lattice widths, so each candidate is timed on the
+    whole batch (direct launches on torch's current stream).  The members'
+    states advance by (steps + warm-up) x len(candidates) steps: re-initialise
+    them afterwards.  Returns (best, {candidate: ms per step})."""
+    timings = {}
+    for c in candidates:
+        b = L.Batch(sims, row_overhead=float(c))
+        try:
+            timings[float(c)] = _event_ms(lambda n: b.step(n, use_graph=False), steps)
+        finally:
+            b.close()
+    best = min(timings, key=timings.get)
+    return best, timings

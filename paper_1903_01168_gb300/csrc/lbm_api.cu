@@ -25,7 +25,7 @@ using namespace lbm;
 namespace {
 
 constexpr int FUSED_W = 128;     // columns per strip = threads per block
-constexpr int FUSED_NSLOT = 5;   // shared-memory row slots per block
+constexpr int FUSED_NSLOT = 4;   // shared-memory row slots per block
 
 thread_local char g_create_err[256] = "";
 
@@ -291,22 +291,25 @@ struct Plan {
 };
 
 constexpr int MIN_PIECE = 8;   // default shortest row range worth a 4-row halo
+constexpr double DEFAULT_ROW_OVERHEAD = 1.0;   // fixed cost of a strip row, in busy warps
 
 void strips_of(std::vector<StripRef> &out, int sim, int nx, int ny, int plan_rows) {
     const int mp = plan_rows > 0 ? plan_rows : MIN_PIECE;
     for (int x0 = 0; x0 < nx; x0 += FUSED_W) out.push_back({sim, x0, std::min(FUSED_W, nx - x0), ny, mp});
 }
 
-// Balanced persistent plan: the strip rows (weighted by the warps a strip
-// keeps busy) are cut into nearly equal shares, in order, so a block may march
-// over the end of one strip and the start of the next.  The share count is
-// max_blocks, or fewer when the strips' own shortest pieces would not fill them.
-Plan balanced_plan(const std::vector<StripRef> &strips, int max_blocks) {
+// Balanced persistent plan: the strip rows are cut into nearly equal shares
+// of cost, in order, so a block may march over the end of one strip and the
+// start of the next.  A row of a strip costs the warps it keeps busy plus a
+// fixed row_overhead (barrier, row loads, edge columns: a narrow strip's row is
+// not proportionally cheaper).  The share count is max_blocks, or fewer when
+// the strips' own shortest pieces would not fill them.
+Plan balanced_plan(const std::vector<StripRef> &strips, int max_blocks, double row_overhead) {
     Plan P;
     double total = 0.0, pieces = 0.0;
     for (const auto &s : strips) {
         const int wc = (s.w + 31) / 32;
-        total += (double)s.ny * wc;
+        total += (double)s.ny * (wc + row_overhead);
         pieces += (double)s.ny * wc / 4.0 / std::max(1, s.min_piece);
     }
     int B = (int)std::min<double>(max_blocks, std::max(1.0, std::floor(pieces)));
@@ -315,7 +318,7 @@ Plan balanced_plan(const std::vector<StripRef> &strips, int max_blocks) {
     int b = 0;
     double acc = 0.0;
     for (const auto &s : strips) {
-        const int wc = (s.w + 31) / 32;
+        const double wc = (s.w + 31) / 32 + row_overhead;
         const int mp = std::max(1, s.min_piece);
         int y = 0;
         while (y < s.ny) {
@@ -406,23 +409,34 @@ cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, con
     }
 }
 
-// Resident fused blocks per SM for a storage type (occupancy query), times SMs.
-int resident_blocks(int storage) {
-    static int cache[3] = {0, 0, 0};
-    if (cache[storage]) return cache[storage];
+// Resident fused blocks per SM for a storage type and collision variant
+// (occupancy query), times SMs.
+int resident_blocks(int storage, int variant) {
+    static int cache[3][4] = {};
+    if (storage < 0 || storage > 2 || variant < 0 || variant > 3) return 1;
+    if (cache[storage][variant]) return cache[storage][variant];
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void *k = storage == ST_F32 ? fused_kernel_ptr<float, 3>()
-                    : storage == ST_F16DEV ? fused_kernel_ptr<__half, 3>() : fused_kernel_ptr<__nv_bfloat16, 3>();
-    // the largest variant (MRT + Hermite source rings) bounds the residency of all
-    const int smem = storage == ST_F32 ? fused_smem<float, 3>() : storage == ST_F16DEV ? fused_smem<__half, 3>()
-                                                                                        : fused_smem<__nv_bfloat16, 3>();
+    const void *k = nullptr;
+    int smem = 0;
+    switch (storage * 4 + variant) {
+#define LBM_RES_CASE(ST, T, CV)                 \
+    case ST * 4 + CV:                            \
+        k = fused_kernel_ptr<T, CV>();           \
+        smem = fused_smem<T, CV>();              \
+        break;
+        LBM_RES_CASE(0, float, 0) LBM_RES_CASE(0, float, 1) LBM_RES_CASE(0, float, 2) LBM_RES_CASE(0, float, 3)
+        LBM_RES_CASE(1, __half, 0) LBM_RES_CASE(1, __half, 1) LBM_RES_CASE(1, __half, 2) LBM_RES_CASE(1, __half, 3)
+        LBM_RES_CASE(2, __nv_bfloat16, 0) LBM_RES_CASE(2, __nv_bfloat16, 1) LBM_RES_CASE(2, __nv_bfloat16, 2)
+        LBM_RES_CASE(2, __nv_bfloat16, 3)
+#undef LBM_RES_CASE
+    }
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, FUSED_W, smem) != cudaSuccess || per < 1) per = 1;
     if (sms < 1) sms = 1;
-    cache[storage] = sms * per;
-    return cache[storage];
+    cache[storage][variant] = sms * per;
+    return cache[storage][variant];
 }
 
 int grid_for(long long n, int threads) {
@@ -634,7 +648,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
     {
         std::vector<StripRef> strips;
         strips_of(strips, 0, nx, ny, p->plan_rows);
-        Plan P = balanced_plan(strips, resident_blocks(p->storage));
+        Plan P = balanced_plan(strips, resident_blocks(p->storage, variant_of(p)), DEFAULT_ROW_OVERHEAD);
         s->n_items = (int)P.items.size();
         s->n_blocks = P.blocks;
         if (cudaMalloc(&s->d_items, P.items.size() * sizeof(WorkItem)) != cudaSuccess ||
@@ -955,7 +969,17 @@ void lbm_destroy(lbm_sim *s) {
 // ------------------------------------------------------------------ batches
 
 lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out) {
-    if (!out || !sims || n <= 0) { set_err(g_create_err, "empty batch"); return LBM_EINVAL; }
+    lbm_batch_opts o{};
+    o.rows_per_item = rows_per_item;
+    o.row_overhead = -1.0f;
+    return lbm_batch_create_ex(sims, n, &o, out);
+}
+
+lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts *opts, lbm_batch **out) {
+    if (!out || !sims || n <= 0 || !opts) { set_err(g_create_err, "empty batch or no options"); return LBM_EINVAL; }
+    const int rows_per_item = opts->rows_per_item;
+    const double row_overhead = opts->row_overhead < 0.0f ? DEFAULT_ROW_OVERHEAD : (double)opts->row_overhead;
+    if (rows_per_item < 0 || !(row_overhead <= 64.0)) { set_err(g_create_err, "batch options out of range"); return LBM_EINVAL; }
     *out = nullptr;
     long long strip_rows = 0;
     for (int i = 0; i < n; i++) {
@@ -986,7 +1010,7 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
                     strips_of(strips, i, sims[i]->nx, sims[i]->ny, sims[i]->p.plan_rows);
             if (strips.empty()) continue;
             Plan P = rows_per_item > 0 ? fixed_plan(strips, rows_per_item)
-                                       : balanced_plan(strips, resident_blocks(st));
+                                       : balanced_plan(strips, resident_blocks(st, cv), row_overhead);
             lbm_batch::Group g{st, cv, (int)items.size(), (int)offs.size(), P.blocks};
             for (int &o : P.off) o += g.item0;
             items.insert(items.end(), P.items.begin(), P.items.end());

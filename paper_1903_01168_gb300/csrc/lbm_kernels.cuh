@@ -137,15 +137,16 @@ struct FusedCfg {
     static constexpr int SLOT_BYTES = ((RHO_BYTES + DEV_BYTES + 127) / 128) * 128;
     static constexpr int RING = W + 2;                       // ring width (columns x0-1 .. x0+W)
     static constexpr bool QRING = (CV & CV_MRT) && (CV & CV_HERMITE);
-    // shared rings (floats).  Stage A of row y+1 may run while slower threads
-    // still do stage B of row y-1, so a ring written by A and read by B for
-    // its own row needs 3 rows (rho_r, rho_b, e_1..8), and one read over rows
-    // y-1..y+1 needs 4 (psi, q u).
+    // shared rings (floats).  rho_r, rho_b and e_1..8 of a column are written
+    // by stage A and read by stage B of the same thread, so two rows suffice
+    // (A(y+1) fills one while B(y) reads the other).  psi and q u are read over
+    // rows y-1..y+1 by the neighbouring threads too, and stage A of row y+1 may
+    // run while slower threads still do stage B of row y-1: 4 rows.
     static constexpr int PSI_OFF = 0;
     static constexpr int RR_OFF = PSI_OFF + 4 * RING;
-    static constexpr int RB_OFF = RR_OFF + 3 * RING;
-    static constexpr int E_OFF = RB_OFF + 3 * RING;
-    static constexpr int QX_OFF = E_OFF + 3 * 8 * RING;
+    static constexpr int RB_OFF = RR_OFF + 2 * RING;
+    static constexpr int E_OFF = RB_OFF + 2 * RING;
+    static constexpr int QX_OFF = E_OFF + 2 * 8 * RING;
     static constexpr int QY_OFF = QX_OFF + (QRING ? 4 * RING : 0);
     static constexpr int RING_FLOATS = QY_OFF + (QRING ? 4 * RING : 0);
     static constexpr int DESC_BYTES = ((int)sizeof(SimDesc) + 127) / 128 * 128;
@@ -170,7 +171,7 @@ struct FusedCfg {
 // y-1..y+1 for the S2I4 gradient.  Stage B reads no source row, so a row's slot
 // is refilled as soon as stage A of the row above has used it.
 template <typename T, int CV, int W, int NSLOT>
-__global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__ descs,
+__global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__ descs,
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ item_off, int n_blocks,
                                                      int step_offset, int *__restrict__ err) {
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
                 }
             } else {
                 const auto L = loader(Y);
-                const int m3 = (Y + 3) % 3;   // Y >= -1
+                const int m3 = (Y + 2) & 1;   // Y >= -1
                 const int r2 = m3 * RING, e2 = m3 * 8 * RING;
                 // interior ring columns x0 .. x0+w-1: one node per thread, full pull
                 if (tid < w) {
@@ -360,7 +361,7 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
             const int x = x0 + tid;
             const int rm = ((y + 3) & 3) * RING, r0 = ((y + 4) & 3) * RING, rp = ((y + 5) & 3) * RING;
             const int c = tid + 1;
-            const int m3 = (y + 3) % 3;
+            const int m3 = (y + 2) & 1;
             const int r2 = m3 * RING, e2 = m3 * 8 * RING;
             Pulled P;
             P.rr = ring_rr[r2 + c];
@@ -394,6 +395,10 @@ __global__ void __launch_bounds__(W, 3) k_step_fused(const SimDesc *__restrict__
         stageA(ya);
         wait_row(ya - 2);
         stageA(ya - 1);
+        __syncthreads();   // rows < ya are no longer read: refill their slots
+        if (tid == 0) {
+            for (; next_issue <= row_last && next_issue <= ya - 1 + NSLOT; ++next_issue) issue(next_issue);
+        }
 
         for (int y = ya; y < yb; ++y) {
             wait_row(y + 2);

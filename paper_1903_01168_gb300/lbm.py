@@ -34,11 +34,17 @@ _STATUS = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA", -4:
 # The C functions every build exports (declared in include/lbm.h).
 ABI_SYMBOLS = (
     "lbm_default_params", "lbm_bytes_required", "lbm_create", "lbm_create_ex", "lbm_init_bubble",
-    "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_set_stop", "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
+    "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_set_stop",
+    "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
     "lbm_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_last_error",
-    "lbm_destroy", "lbm_batch_create", "lbm_batch_step", "lbm_batch_items", "lbm_batch_destroy",
+    "lbm_destroy", "lbm_batch_create", "lbm_batch_create_ex", "lbm_batch_step", "lbm_batch_items",
+    "lbm_batch_destroy",
     "lbm_step_noalloc",
 )
+
+
+class lbm_batch_opts(ctypes.Structure):
+    _fields_ = [("rows_per_item", ctypes.c_int), ("row_overhead", ctypes.c_float)]
 
 
 class lbm_params(ctypes.Structure):
@@ -126,6 +132,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbm_destroy.restype = None
     L.lbm_step_noalloc.argtypes = [pp, i, i, vp, st, ctypes.c_longlong, l, vp]
     L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
+    L.lbm_batch_create_ex.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(lbm_batch_opts), ctypes.POINTER(vp)]
     L.lbm_batch_step.argtypes = [vp, l, i]
     L.lbm_batch_items.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
@@ -259,10 +266,14 @@ def lbm_step_noalloc(p: lbm_params, nx: int, ny: int, state_ptr: int, nbytes: in
                                    ctypes.c_void_p(stream)))
 
 
-def lbm_batch_create(sims, rows_per_item: int = 0) -> int:
+def lbm_batch_create(sims, rows_per_item: int = 0, row_overhead: float | None = None) -> int:
     arr = (ctypes.c_void_p * len(sims))(*sims)
     h = ctypes.c_void_p()
-    _check(load().lbm_batch_create(arr, len(sims), rows_per_item, ctypes.byref(h)))
+    if row_overhead is None:
+        _check(load().lbm_batch_create(arr, len(sims), rows_per_item, ctypes.byref(h)))
+    else:
+        opts = lbm_batch_opts(rows_per_item=rows_per_item, row_overhead=row_overhead)
+        _check(load().lbm_batch_create_ex(arr, len(sims), ctypes.byref(opts), ctypes.byref(h)))
     return h.value
 
 
@@ -376,9 +387,11 @@ class Simulation:
 class Batch:
     """Several simulations advanced together, one launch per step."""
 
-    def __init__(self, sims, rows_per_item: int = 0):
+    def __init__(self, sims, rows_per_item: int = 0, row_overhead: float | None = None):
+        """rows_per_item > 0: fixed plan; row_overhead: planner's fixed cost of a
+        strip row in busy warps (None: library default)."""
         self.sims = list(sims)
-        self.h = lbm_batch_create([s.h for s in self.sims], rows_per_item)
+        self.h = lbm_batch_create([s.h for s in self.sims], rows_per_item, row_overhead)
 
     @property
     def items(self) -> int:

@@ -55,6 +55,16 @@ def test_host_only_calls():
     assert L.lbm_bytes_required(4, 32, L.lbm_default_params()) == 0
 
 
+def test_batch_options_are_checked_before_any_device_call():
+    lib = L.load()
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)(None)
+    opts = L.lbm_batch_opts(rows_per_item=0, row_overhead=1.0)
+    assert lib.lbm_batch_create_ex(arr, 0, ctypes.byref(opts), ctypes.byref(h)) == L.LBM_EINVAL
+    assert lib.lbm_batch_create_ex(arr, 1, None, ctypes.byref(h)) == L.LBM_EINVAL
+    assert h.value is None
+
+
 def test_binding_refuses_missing_library(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "_lib", None)
     monkeypatch.setattr(B, "LIB", str(tmp_path / "nope.so"))

@@ -60,3 +60,37 @@ def test_tuned_batch_equals_alone():
     b.close()
     for s in sims:
         s.close()
+
+
+def test_row_overhead_never_changes_results():
+    """The planner's row cost only moves rows between thread blocks: batches
+    planned with every candidate cost reach bit-identical states, and the tuner
+    returns one of the candidates."""
+    specs = [(96, 64), (160, 200), (300, 90), (32, 128)]
+
+    def members():
+        out = []
+        for nx, ny in specs:
+            s = L.Simulation(nx, ny, torch_memory=True, gamma=10.0, sigma=0.005, storage=1)
+            s.init_fields(*W.bubble_fields(nx, ny, nx / 2, ny / 2, ny / 4, 10.0))
+            out.append(s)
+        return out
+
+    ref = None
+    for c in A.ROW_OVERHEAD_CANDIDATES:
+        sims = members()
+        b = L.Batch(sims, row_overhead=c)
+        b.step(17, use_graph=False)
+        sims[0].synchronize()
+        states = [s.save_state() for s in sims]
+        b.close()
+        for s in sims:
+            s.close()
+        if ref is None:
+            ref = states
+        assert states == ref
+    sims = members()
+    best, timings = A.tune_row_overhead(sims, steps=4)
+    assert best in A.ROW_OVERHEAD_CANDIDATES and set(timings) == set(A.ROW_OVERHEAD_CANDIDATES)
+    for s in sims:
+        s.close()
