@@ -438,26 +438,38 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
     const bool force = (p.gx != 0.0f) || (p.gy != 0.0f);
 
     // velocity part of the colour-blind equilibrium, sum_k N^{k(e)}_i - R_i
-    // (Eq. (eq:equilibrium) / (eq:equilibrium_hermite)), and the Guo source
+    // (Eq. (eq:equilibrium) / (eq:equilibrium_hermite)), and the Guo source,
+    // formed per opposite pair (i, OPP(i)) from the part even in c_i and the
+    // part odd in c_i (c_OPP(i) = -c_i)
     const float usq = ux * ux + uy * uy;
     const float herm = HERMITE ? 0.5f * (rr * p.herm_r + rb * p.herm_b) : 0.0f;
     const float Gx = rho * p.gx, Gy = rho * p.gy;
     const float uG = ux * Gx + uy * Gy;
     float weq[9], src[9];
+    weq[0] = WT(0) * rho * (-1.5f * usq);
+    src[0] = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
+    for (int i : {1, 2, 5, 6}) {
+        const int j = OPP(i);
         const float cu = CX(i) * ux + CY(i) * uy;
-        float lin = rho * 3.0f * cu;
-        if (HERMITE && C2(i) > 0) lin += 3.0f * cu * (3.0f * C2(i) - 4.0f) * herm;
-        weq[i] = WT(i) * (lin + rho * (4.5f * cu * cu - 1.5f * usq));
-        src[i] = 0.0f;
+        const float even = WT(i) * rho * (4.5f * cu * cu - 1.5f * usq);
+        float odd = WT(i) * 3.0f * rho * cu;
+        if (HERMITE) odd += WT(i) * 3.0f * cu * (3.0f * C2(i) - 4.0f) * herm;
+        weq[i] = even + odd;
+        weq[j] = even - odd;
+        src[i] = src[j] = 0.0f;
     }
     if (force) {
+        src[0] = WT(0) * (-3.0f * uG);
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
+        for (int i : {1, 2, 5, 6}) {
+            const int j = OPP(i);
             const float cu = CX(i) * ux + CY(i) * uy;
             const float cG = CX(i) * Gx + CY(i) * Gy;
-            src[i] = WT(i) * (3.0f * (cG - uG) + 9.0f * cu * cG);
+            const float even = WT(i) * (9.0f * cu * cG - 3.0f * uG);
+            const float odd = WT(i) * 3.0f * cG;
+            src[i] = even + odd;
+            src[j] = even - odd;
         }
     }
 
@@ -525,28 +537,36 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
     const float fr = rr * inv_rho, fb = rb * inv_rho;
     const float mix = rr * rb * inv_rho;
     const float F2 = Fx * Fx + Fy * Fy;
+    // per |c|^2 class: shift of the stored deviations
+    const float sh1 = mix * (p.phi_b[1] - p.phi_r[1]), sh2 = mix * (p.phi_b[2] - p.phi_r[2]);
     if (F2 > 0.0f) {
         // Eq. (eq:perturbation), one A/2 term per colour: A |F| [W (F.c)^2/|F|^2 - B]
+        // (even in c_i), and the recolouring flux (odd in c_i)
         const float invFn = rsqrtf(F2);
         const float Fn = F2 * invFn;
         const float A = p.a_coef * w;
         const float pa = A * invFn, pb = A * Fn;
         const float kk = p.beta * mix * inv_rho * invFn;   // beta rr rb / rho^2 / |F|
+        // cos(phi_i) = c_i.F / (|c_i| |F|); rest_i = rr phi^r_i + rb phi^b_i
+        const float k1 = kk * (rr * p.phi_r[1] + rb * p.phi_b[1]);
+        const float k2 = kk * 0.70710678118654752f * (rr * p.phi_r[2] + rb * p.phi_b[2]);
 #pragma unroll
-        for (int i = 1; i < 9; i++) {
+        for (int i : {1, 2, 5, 6}) {
+            const int j = OPP(i);
             const float Fc = CX(i) * Fx + CY(i) * Fy;
-            const float E = e[i] + (pa * WT(i) * Fc * Fc - pb * BP(i));
-            const float inv_c = C2(i) == 1 ? 1.0f : 0.70710678118654752f;
-            const float rest = rr * p.phi_r[C2(i)] + rb * p.phi_b[C2(i)];
-            const float term = kk * Fc * inv_c * rest;   // cos(phi_i) = c_i.F / (|c_i| |F|)
-            const float sh = mix * (p.phi_b[C2(i)] - p.phi_r[C2(i)]);
-            dr[i] = sh + fr * E + term;
-            db[i] = -sh + fb * E - term;
+            const float pert = pa * WT(i) * Fc * Fc - pb * BP(i);
+            const float term = (C2(i) == 1 ? k1 : k2) * Fc;
+            const float sh = C2(i) == 1 ? sh1 : sh2;
+            const float Ei = e[i] + pert, Ej = e[j] + pert;
+            dr[i] = sh + fr * Ei + term;
+            dr[j] = sh + fr * Ej - term;
+            db[i] = -sh + fb * Ei - term;
+            db[j] = -sh + fb * Ej + term;
         }
     } else {
 #pragma unroll
         for (int i = 1; i < 9; i++) {
-            const float sh = mix * (p.phi_b[C2(i)] - p.phi_r[C2(i)]);
+            const float sh = C2(i) == 1 ? sh1 : sh2;
             dr[i] = sh + fr * e[i];
             db[i] = -sh + fb * e[i];
         }

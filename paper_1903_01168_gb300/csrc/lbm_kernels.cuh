@@ -137,16 +137,12 @@ struct FusedCfg {
     static constexpr int SLOT_BYTES = ((RHO_BYTES + DEV_BYTES + 127) / 128) * 128;
     static constexpr int RING = W + 2;                       // ring width (columns x0-1 .. x0+W)
     static constexpr bool QRING = (CV & CV_MRT) && (CV & CV_HERMITE);
-    // shared rings (floats).  rho_r, rho_b and e_1..8 of a column are written
-    // by stage A and read by stage B of the same thread, so two rows suffice
-    // (A(y+1) fills one while B(y) reads the other).  psi and q u are read over
-    // rows y-1..y+1 by the neighbouring threads too, and stage A of row y+1 may
-    // run while slower threads still do stage B of row y-1: 4 rows.
+    // shared rings (floats) of what neighbouring threads read: psi and q u over
+    // rows y-1..y+1.  Stage A of row y+1 may run while slower threads still do
+    // stage B of row y-1, so they hold 4 rows.  The node's own rho_r, rho_b and
+    // e_1..8 stay in the registers of the thread that pulled them.
     static constexpr int PSI_OFF = 0;
-    static constexpr int RR_OFF = PSI_OFF + 4 * RING;
-    static constexpr int RB_OFF = RR_OFF + 2 * RING;
-    static constexpr int E_OFF = RB_OFF + 2 * RING;
-    static constexpr int QX_OFF = E_OFF + 2 * 8 * RING;
+    static constexpr int QX_OFF = PSI_OFF + 4 * RING;
     static constexpr int QY_OFF = QX_OFF + (QRING ? 4 * RING : 0);
     static constexpr int RING_FLOATS = QY_OFF + (QRING ? 4 * RING : 0);
     static constexpr int DESC_BYTES = ((int)sizeof(SimDesc) + 127) / 128 * 128;
@@ -164,12 +160,14 @@ struct FusedCfg {
 //
 // Per segment the block marches up rows ya .. yb-1 of a strip of w <= W
 // columns.  Source rows arrive by TMA into a ring of NSLOT shared slots.
-// Iteration y first pulls ring row y+1 (stage A: new colour densities, colour
-// field and the colour-blind non-rest parts e_i of every node of that row, plus
-// one column each side), then collides row y (stage B) from what stage A left
-// in the shared rings: its own densities and e_i, and the colour field of rows
-// y-1..y+1 for the S2I4 gradient.  Stage B reads no source row, so a row's slot
-// is refilled as soon as stage A of the row above has used it.
+// Iteration y first pulls row y+1 (stage A: new colour densities, colour field
+// and the colour-blind non-rest parts e_i of every node of that row; the colour
+// field also one column each side), then collides row y (stage B) from the
+// densities and e_i that the same thread pulled one iteration earlier (kept in
+// registers) and the colour field of rows y-1..y+1 in a shared ring (S2I4
+// gradient).  Stage B reads no source row, so a row's slot is refilled as soon
+// as stage A of the row above has used it.  One block runs 4 warps; 4 blocks
+// share an SM (128 registers per thread, shared memory per block below 56 KB).
 template <typename T, int CV, int W, int NSLOT>
 __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__ descs,
                                                      const WorkItem *__restrict__ items,
@@ -188,9 +186,6 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
     unsigned char *slots = smem + Cfg::DESC_BYTES;
     float *rings = reinterpret_cast<float *>(slots + NSLOT * Cfg::SLOT_BYTES);
     float *ring_psi = rings + Cfg::PSI_OFF;
-    float *ring_rr = rings + Cfg::RR_OFF;
-    float *ring_rb = rings + Cfg::RB_OFF;
-    float *ring_e = rings + Cfg::E_OFF;
     float *ring_qx = rings + Cfg::QX_OFF;
     float *ring_qy = rings + Cfg::QY_OFF;
     uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(rings) + Cfg::RING_BYTES);
@@ -284,7 +279,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
         };
 
         // stage A: ring row Y, columns x0-1 .. x0+w
-        auto stageA = [&](int Y) {
+        auto stageA = [&](int Y, Pulled &out) {
             const int rs = ((Y + 4) & 3) * RING;
             if (wall_y && (Y < 0 || Y >= ny)) {
                 const int Yn = Y < 0 ? 0 : ny - 1;
@@ -304,8 +299,6 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
                 }
             } else {
                 const auto L = loader(Y);
-                const int m3 = (Y + 2) & 1;   // Y >= -1
-                const int r2 = m3 * RING, e2 = m3 * 8 * RING;
                 // interior ring columns x0 .. x0+w-1: one node per thread, full pull
                 if (tid < w) {
                     const int c = tid + 1;
@@ -313,10 +306,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
                     Pulled P;
                     pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
                     ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
-                    ring_rr[r2 + c] = P.rr;
-                    ring_rb[r2 + c] = P.rb;
-#pragma unroll
-                    for (int i = 1; i < 9; i++) ring_e[e2 + (i - 1) * RING + c] = P.e[i];
+                    out = P;
                     if (HERMITE_SRC) {
                         const NodeMoments m = node_moments(p, P);
                         const float q = p.q_r * m.rr + p.q_b * m.rb;
@@ -356,22 +346,15 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
         };
 
         // stage B: collide row y from the rings
-        auto stageB = [&](int y) {
+        auto stageB = [&](int y, const Pulled &Pin) {
             if (tid >= w) return;
             const int x = x0 + tid;
             const int rm = ((y + 3) & 3) * RING, r0 = ((y + 4) & 3) * RING, rp = ((y + 5) & 3) * RING;
             const int c = tid + 1;
-            const int m3 = (y + 2) & 1;
-            const int r2 = m3 * RING, e2 = m3 * 8 * RING;
-            Pulled P;
-            P.rr = ring_rr[r2 + c];
-            P.rb = ring_rb[r2 + c];
+            Pulled P = Pin;
             float e0 = 0.0f;
 #pragma unroll
-            for (int i = 1; i < 9; i++) {
-                P.e[i] = ring_e[e2 + (i - 1) * RING + c];
-                e0 += P.e[i];
-            }
+            for (int i = 1; i < 9; i++) e0 += P.e[i];
             P.e[0] = -e0;
             auto ring = [&](const float *f) {
                 return [=](int dx, int dy) { return f[(dy < 0 ? rm : (dy == 0 ? r0 : rp)) + c + dx]; };
@@ -392,9 +375,10 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
         wait_row(ya - 1);
         wait_row(ya);
         wait_row(ya + 1);
-        stageA(ya);
+        Pulled Pc, Pn;   // pulled state of this thread's node in rows y and y + 1
+        stageA(ya, Pc);
         wait_row(ya - 2);
-        stageA(ya - 1);
+        stageA(ya - 1, Pn);
         __syncthreads();   // rows < ya are no longer read: refill their slots
         if (tid == 0) {
             for (; next_issue <= row_last && next_issue <= ya - 1 + NSLOT; ++next_issue) issue(next_issue);
@@ -402,14 +386,15 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
 
         for (int y = ya; y < yb; ++y) {
             wait_row(y + 2);
-            stageA(y + 1);
+            stageA(y + 1, Pn);
             __syncthreads();
             if (s_bad) break;
             if (tid == 0) {
                 // rows <= y are no longer read (stage A(y+1) was their last reader)
                 for (; next_issue <= row_last && next_issue <= y + NSLOT; ++next_issue) issue(next_issue);
             }
-            stageB(y);
+            stageB(y, Pc);
+            Pc = Pn;
         }
 
         if (s_bad) {
