@@ -195,10 +195,12 @@ void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     h.ghost = GHOST;
     h.pitch_r = pitch_rho(nx);
     h.pitch_d = pitch_dev(nx, p->storage);
-    h.rho_plane = (long long)ny * h.pitch_r;
-    h.rho_buf = 2LL * h.rho_plane;
-    h.dev_plane = (long long)ny * h.pitch_d;
-    h.dev_buf = 16LL * h.dev_plane;
+    h.rho_plane = h.pitch_r;
+    h.rho_row = 2LL * h.pitch_r;
+    h.rho_buf = (long long)ny * h.rho_row;
+    h.dev_plane = h.pitch_d;
+    h.dev_row = 16LL * h.pitch_d;
+    h.dev_buf = (long long)ny * h.dev_row;
     Phys &f = h.ph;
     f.nx = nx;
     f.ny = ny;
@@ -255,21 +257,22 @@ lbm_status encode_tmap(lbm_sim *s) {
                                    : s->p.storage == ST_F16DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint32_t box_w = FUSED_W + 2 * (16 / es);   // halo columns loaded: 4 (FP32) or 8 (16-bit)
-    cuuint32_t estr[3] = {1, 1, 1};
+    // rows of planes over both buffers: [2][ny][planes] -> one 2D row index
+    cuuint32_t estr[2] = {1, 1};
     {
-        cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch_r, (cuuint64_t)s->ny, 4};
-        cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch_r * 4, (cuuint64_t)s->h.rho_plane * 4};
-        cuuint32_t box[3] = {box_w, 1, 2};
-        CUresult r = enc(&s->h.tmap_rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->h.rho, dims, strides, box, estr,
+        cuuint64_t dims[2] = {(cuuint64_t)s->h.pitch_r, (cuuint64_t)s->ny * 2 * 2};
+        cuuint64_t strides[1] = {(cuuint64_t)s->h.pitch_r * 4};
+        cuuint32_t box[2] = {box_w, 2};
+        CUresult r = enc(&s->h.tmap_rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s->h.rho, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { set_err(s->err, "cuTensorMapEncodeTiled (rho) failed (%d)", (int)r); return LBM_ECUDA; }
     }
     {
-        cuuint64_t dims[3] = {(cuuint64_t)s->h.pitch_d, (cuuint64_t)s->ny, 32};
-        cuuint64_t strides[2] = {(cuuint64_t)s->h.pitch_d * es, (cuuint64_t)s->h.dev_plane * es};
-        cuuint32_t box[3] = {box_w, 1, 16};
-        CUresult r = enc(&s->h.tmap_dev, dt, 3, s->h.dev, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        cuuint64_t dims[2] = {(cuuint64_t)s->h.pitch_d, (cuuint64_t)s->ny * 2 * 16};
+        cuuint64_t strides[1] = {(cuuint64_t)s->h.pitch_d * es};
+        cuuint32_t box[2] = {box_w, 16};
+        CUresult r = enc(&s->h.tmap_dev, dt, 2, s->h.dev, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) { set_err(s->err, "cuTensorMapEncodeTiled (dev) failed (%d)", (int)r); return LBM_ECUDA; }

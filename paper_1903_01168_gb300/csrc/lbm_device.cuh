@@ -34,9 +34,13 @@ enum : int { ERR_TIMEOUT = 1, ERR_BADITEM = 2, ERR_ALIGN = 4 };
 // deviation d^k_0 = -sum_{i>=1} d^k_i is implied, so every node's deviations
 // sum to zero exactly, a colour that is absent is an exact zero, and all
 // quantities the step manipulates are small where a phase is at rest.
-//   rho planes: [2 buffers][2 colours][ny][pitch_r]          float
-//   dev planes: [2 buffers][16 = colour * 8 + (i - 1)][ny][pitch_d]   T
-// Rows keep `ghost` columns on each side (periodic copies in x).  The tensor
+//   rho planes: [2 buffers][ny][2 colours][pitch_r]          float
+//   dev planes: [2 buffers][ny][16 = colour * 8 + (i - 1)][pitch_d]   T
+// i.e. the planes of one lattice row lie next to each other, so that reading
+// or writing a row of a strip touches one contiguous stretch of memory per
+// array (a planar [plane][ny] layout spreads it over 18 distant pages and
+// streams markedly slower).  Rows keep `ghost` columns on each side (periodic
+// copies in x).  The tensor
 // maps come first so that they keep the 64-byte alignment TMA requires.
 // Per-simulation constants the node operators read; kernels copy this struct
 // into registers once.
@@ -56,12 +60,12 @@ struct Phys {
 };
 
 struct alignas(128) SimDesc {
-    CUtensorMap tmap_rho;      // 3D {pitch_r, ny, 4} box {W + 2 ghost, 1, 2}
-    CUtensorMap tmap_dev;      // 3D {pitch_d, ny, 32} box {W + 2 ghost, 1, 16}
+    CUtensorMap tmap_rho;      // 2D {pitch_r, 2 * ny * 2} box {W + 2 halo, 2}: one row's 2 planes
+    CUtensorMap tmap_dev;      // 2D {pitch_d, 2 * ny * 16} box {W + 2 halo, 16}: one row's 16 planes
     float *rho;
     void *dev;
-    long long rho_plane, rho_buf;   // element strides
-    long long dev_plane, dev_buf;
+    long long rho_plane, rho_row, rho_buf;   // element strides of a plane, a row, a buffer
+    long long dev_plane, dev_row, dev_buf;
     long long t0;              // time of the state when a launch chunk starts
     long long t_end;           // steps that would start at t >= t_end are skipped
     int pitch_r, pitch_d, ghost;
@@ -127,9 +131,9 @@ struct NodeStore {
     int mirror_l;      // -nx when x also lives in the left ghost columns, else 0
 
     __device__ __forceinline__ NodeStore(const SimDesc &d, const Phys &p, int b, int x, int y) {
-        rho = d.rho + b * d.rho_buf + (long long)y * d.pitch_r + d.ghost + x;
+        rho = d.rho + b * d.rho_buf + (long long)y * d.rho_row + d.ghost + x;
         rho_plane = d.rho_plane;
-        dev = reinterpret_cast<T *>(d.dev) + b * d.dev_buf + (long long)y * d.pitch_d + d.ghost + x;
+        dev = reinterpret_cast<T *>(d.dev) + b * d.dev_buf + (long long)y * d.dev_row + d.ghost + x;
         dev_plane = d.dev_plane;
         const bool per = p.bc_x == BC_PERIODIC;
         mirror_r = (per && x < d.ghost) ? p.nx : 0;
@@ -631,6 +635,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (clock64() - start > limit_cycles) return false;
     }
     return true;
+}
+
+// 2D tiled TMA load of one box into shared memory, completion on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(tm), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // 3D tiled TMA load of one box into shared memory, completion on `bar`.

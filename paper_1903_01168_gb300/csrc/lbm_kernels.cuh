@@ -29,23 +29,23 @@ template <typename T>
 struct GlobalLoader {
     const float *rho0;   // &rho[b][0][0][0] (interior column 0)
     const T *dev0;       // &dev[b][0][0][0]
-    long long rho_plane, dev_plane;
-    int pitch_r, pitch_d, ny;
+    long long rho_plane, dev_plane, rho_row, dev_row;
+    int ny;
     __device__ __forceinline__ GlobalLoader(const SimDesc &d, int b) {
         rho0 = d.rho + b * d.rho_buf + d.ghost;
         dev0 = reinterpret_cast<const T *>(d.dev) + b * d.dev_buf + d.ghost;
         rho_plane = d.rho_plane;
         dev_plane = d.dev_plane;
-        pitch_r = d.pitch_r;
-        pitch_d = d.pitch_d;
+        rho_row = d.rho_row;
+        dev_row = d.dev_row;
         ny = d.ph.ny;
     }
     __device__ __forceinline__ int wrap(int ys) const { return ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys); }
     __device__ __forceinline__ float rho(int k, int xs, int ys) const {
-        return rho0[k * rho_plane + (long long)wrap(ys) * pitch_r + xs];
+        return rho0[k * rho_plane + (long long)wrap(ys) * rho_row + xs];
     }
     __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
-        return Codec<T>::dec(dev0[(k * 8 + i - 1) * dev_plane + (long long)wrap(ys) * pitch_d + xs]);
+        return Codec<T>::dec(dev0[(k * 8 + i - 1) * dev_plane + (long long)wrap(ys) * dev_row + xs]);
     }
 };
 
@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
             unsigned char *dst = slots + s * Cfg::SLOT_BYTES;
             const int xb = x0 + (Cfg::GMEM - G);   // element index of column x0 - G in the padded row
             mbar_arrive_expect_tx(&bars[s], Cfg::TX_BYTES);
-            tma_load_3d(dst, &gd->tmap_rho, &bars[s], xb, yr, bsrc * 2);
-            tma_load_3d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], xb, yr, bsrc * 16);
+            const int brow = bsrc * ny + yr;   // row index over both buffers
+            tma_load_2d(dst, &gd->tmap_rho, &bars[s], xb, brow * 2);
+            tma_load_2d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], xb, brow * 16);
         };
         int next_issue = row_first;   // meaningful on thread 0 only
         if (tid == 0) {
