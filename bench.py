@@ -259,24 +259,10 @@ def main():
     stream = torch.cuda.Stream()
     sim_params = [dict(gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta,
                        storage=storage, gx=sp.gx, bc_y=sp.bc_y) for sp in specs]
-    tuned = None
-    if not args.no_autotune:
-        from paper_1903_01168_gb300.autotune import Autotuner
-        tuner = Autotuner()
-        ta = time.perf_counter()
-        with torch.cuda.stream(stream):
-            tuned = tuner.tune_batch([(sp.nx, sp.ny, kw) for sp, kw in zip(specs, sim_params)])
-        tune_s = time.perf_counter() - ta
-        sim_params = [tuner.params_for(sp.nx, sp.ny, True, **kw) for sp, kw in zip(specs, sim_params)]
     sims = []
     with torch.cuda.stream(stream):
         for sp, kw in zip(specs, sim_params):
-            s = L.Simulation(sp.nx, sp.ny, torch_memory=True, **kw)
-            if sp.geometry == "bubble":
-                s.init_bubble(*sp.bubble)
-            else:
-                s.init_slug(int(sp.slug[0]), sp.slug[1], sp.slug[2], True)
-            sims.append(s)
+            sims.append(L.Simulation(sp.nx, sp.ny, torch_memory=True, **kw))
 
     def init_all():
         for sp, s in zip(specs, sims):
@@ -285,15 +271,20 @@ def main():
             else:
                 s.init_slug(int(sp.slug[0]), sp.slug[1], sp.slug[2], True)
 
-    row_overhead = None
+    tuned = None
     with torch.cuda.stream(stream):
-        if tuned is not None:
-            from paper_1903_01168_gb300.autotune import tune_row_overhead
+        init_all()
+        if not args.no_autotune:
+            # per size class plan_rows and plan options, timed on this batch, then a fresh start
+            from paper_1903_01168_gb300.autotune import Autotuner
             ta = time.perf_counter()
-            row_overhead, oh_timings = tune_row_overhead(sims)
-            tune_s += time.perf_counter() - ta
+            tuned = Autotuner().tune_batch(sims)
+            tune_s = time.perf_counter() - ta
             init_all()
-        batch = L.Batch(sims, row_overhead=row_overhead)
+            batch = L.Batch(sims, row_overhead=tuned["row_overhead"], plan=tuned["plan"],
+                            member_plan_rows=tuned["member_plan_rows"])
+        else:
+            batch = L.Batch(sims)
     nodes = sum(sp.nx * sp.ny for sp in specs)
 
     def barrier():
@@ -374,8 +365,9 @@ def main():
                    "kernel": "k_step_fused (batched, graph)",
                    "work_items": batch.items,
                    "autotune": (None if tuned is None else
-                                {"seconds": round(tune_s, 2), "row_overhead": row_overhead,
-                                 "plan_rows": {k.removeprefix("batch-"): v["plan_rows"] for k, v in tuned.items()}}),
+                                {"seconds": round(tune_s, 2), "row_overhead": tuned["row_overhead"],
+                                 "plan": {0: "auto", 1: "balanced", 2: "split"}[tuned["plan"]],
+                                 "plan_rows": {k: v for k, v in tuned["classes"].items() if v != 8}}),
                    "l2": f"inputs larger than L2: {2 * algo_bytes / 2e6:.0f} MB of state touched per step",
                    "parallelism":
                    "replicas only" if world > 1 else "single GPU"},

@@ -67,6 +67,17 @@ typedef enum { LBM_INLET_ALTERNATE = 0, LBM_INLET_LAYERED = 1 } lbm_inlet_mode;
  * reference kernel pair (moments pass + collide pass, with a scratch field). */
 typedef enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_FUSED = 1, LBM_KERNEL_TWOPASS = 2 } lbm_kernel;
 
+/* How the strip rows of a launch are shared among thread blocks.  Every plan
+ * gives the same results; only the speed differs. */
+typedef enum {
+    LBM_PLAN_AUTO = 0,      /* SPLIT when there are no more 128-column strips than
+                               resident blocks, else BALANCED (the default) */
+    LBM_PLAN_BALANCED = 1,  /* equal shares of row cost; a block may march over
+                               several segments */
+    LBM_PLAN_SPLIT = 2      /* one segment per block, the costliest segment as cheap
+                               as the block count allows */
+} lbm_plan_kind;
+
 typedef struct {
     double gamma;        /* density ratio rho_r^0 / rho_b^0 >= 1 (Eq. (eq:gammaAlphaBeta)) */
     double alpha_b;      /* rest fraction of blue, 0 < alpha_b < 1 (paper: 0.2); alpha_r =
@@ -94,6 +105,7 @@ typedef struct {
                             batch; larger values trade parallelism for less halo
                             re-reading.  Never changes results, only speed (the
                             Python autotuner picks it per lattice size class). */
+    int plan;            /* lbm_plan_kind of this lattice's own launches (0 = AUTO) */
 } lbm_params;
 
 /* FP64 diagnostics of the state at the current time t (sums over all nodes). */
@@ -235,22 +247,38 @@ lbm_status lbm_step_noalloc(const lbm_params *p, int nx, int ny, void *state, si
  * kernel launch per time step and storage / collision type (types run
  * concurrently on streams of the batch, joined into the stream of sims[0]).
  * rows_per_item > 0 cuts every strip into pieces of that many rows, one per
- * thread block; 0 spreads the rows of all members evenly over the resident
- * thread blocks, no segment of a member shorter than its plan_rows.
+ * thread block; 0 shares the rows of all members among the resident thread
+ * blocks (LBM_PLAN_AUTO of lbm_batch_create_ex), no segment of a member shorter
+ * than its plan_rows.
  * The simulations stay owned by the caller and must outlive the batch. */
 lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_batch **out);
 
+
 /* Work-plan options of a batch. */
 typedef struct {
-    int rows_per_item;   /* > 0: fixed plan, as in lbm_batch_create; 0: balanced plan */
-    float row_overhead;  /* balanced plan: cost of one strip row = the warps it keeps busy
-                            (1..4) + row_overhead; < 0 selects the library default (1).
-                            Changes only which block updates which rows, never results. */
+    int rows_per_item;   /* > 0: fixed plan, as in lbm_batch_create (plan is ignored) */
+    float row_overhead;  /* cost of one strip row = the warps it keeps busy (1..4) +
+                            row_overhead; < 0 selects the library default (1) */
+    int plan;            /* lbm_plan_kind */
+    const int *member_plan_rows; /* NULL, or n values (>= 0, 0 = 8) used instead of each
+                            member's own plan_rows; read during the call only */
 } lbm_batch_opts;
 
 /* lbm_batch_create with explicit plan options (opts must not be NULL).
- * LBM_EINVAL for rows_per_item < 0 or row_overhead > 64. */
+ * LBM_EINVAL for rows_per_item < 0, row_overhead > 64, an unknown plan or a
+ * member_plan_rows value out of range. */
 lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts *opts, lbm_batch **out);
+
+/* Host only (no device call): the work plan a batch of n lattices of sizes
+ * nx[i] x ny[i] would get with these options and max_blocks resident thread
+ * blocks (the library queries that number from the device; pass any positive
+ * value here).  plan_rows: NULL or the members' plan_rows (opts->member_plan_rows
+ * takes precedence).  Sets *n_items and *n_blocks and writes the first
+ * `capacity` items as 6 ints each: member, first column, width (<= 128), first
+ * row, end row, thread block.  Items of one block are listed in the order the
+ * block runs them.  LBM_EINVAL for invalid sizes or options. */
+lbm_status lbm_plan_preview(const int *nx, const int *ny, const int *plan_rows, int n, const lbm_batch_opts *opts,
+                            int max_blocks, int *n_items, int *n_blocks, int *items, int capacity);
 
 /* Advance every simulation of the batch by n steps; with use_graph != 0 the
  * launches are captured once into a CUDA graph of n steps and replayed on

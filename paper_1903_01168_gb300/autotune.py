@@ -12,10 +12,12 @@ wins.
 
 A size class is (storage type, collision, equilibrium, nx and ny rounded up to
 powers of two).  Tuning a single lattice times it alone; tuning for a batch
-times the members of each class together as a small batch, so the choice is the
-one that pays inside a batched launch.  A whole batch also gets its planner's
-row cost model tuned (`tune_row_overhead`): how much of a full strip row a
-narrow strip's row costs, which decides how many rows each block receives.
+times the whole batch while the plan_rows of one class at a time varies, so the
+choice is the one that pays inside that batched launch.  A whole batch also gets
+its work plan
+tuned (`tune_plan`): one segment per block (split) or equal shares of row cost
+over several segments per block (balanced), each with a row cost model (how
+much of a full strip row a narrow strip's row costs).
 
 The plan never changes what a node computes, so every candidate gives
 bit-identical results; only the time differs.
@@ -30,7 +32,9 @@ from . import lbm as L
 
 PLAN_CANDIDATES = (8, 16, 32, 64)
 ROW_OVERHEAD_CANDIDATES = (0.0, 0.5, 1.0, 2.0, 4.0)
-CLASS_SAMPLE = 4          # members of a class timed together when tuning a batch
+# (plan kind, row overhead) pairs timed on a whole batch
+PLAN_OPTION_CANDIDATES = tuple((L.LBM_PLAN_SPLIT, o) for o in (0.0, 1.0, 4.0)) + \
+    tuple((L.LBM_PLAN_BALANCED, o) for o in ROW_OVERHEAD_CANDIDATES)
 
 
 def _pow2(n: int) -> int:
@@ -117,31 +121,50 @@ class Autotuner:
             self._record(key, timings)
         return self.table[key]
 
-    def tune_batch(self, members) -> dict:
-        """members: list of (nx, ny, params) that will run as one batch.  For each
-        size class among them, time up to CLASS_SAMPLE of its members together as
-        a batch under every candidate plan_rows; returns {class: choice}."""
-        by_class: dict[str, list] = {}
-        for nx, ny, params in members:
-            by_class.setdefault("batch-" + class_of(nx, ny, params), []).append((nx, ny, params))
-        for key, group in by_class.items():
-            if key in self.table:
-                continue
-            sample = group[:CLASS_SAMPLE]
-            timings = []
-            for c in self._choices(batched=True):
-                sims = [_start(nx, ny, params, c) for nx, ny, params in sample]
-                try:
-                    b = L.Batch(sims)
-                    try:
-                        timings.append((_event_ms(lambda n: b.step(n, use_graph=False), self.steps), c))
-                    finally:
-                        b.close()
-                finally:
-                    for s in sims:
-                        s.close()
-            self._record(key, timings)
-        return {k: self.table[k] for k in by_class}
+    def tune_batch(self, sims, steps: int = 20, gain: float = 0.02) -> dict:
+        """Per size class plan_rows and the plan options of one batch, timed on
+        the batch itself (the members of a class alone would neither fill the GPU
+        nor share it as they do in the batch).
+
+        Coordinate descent: start from the default plan for every member; for
+        each size class (largest share of nodes first) try every candidate
+        plan_rows for that class's members with the others fixed, and keep one
+        that is at least `gain` faster.  Then time the plan kinds and row costs
+        (`tune_plan`) with the chosen plan_rows.  The members' states advance:
+        re-initialise them afterwards.  Returns {"classes": {class: plan_rows},
+        "member_plan_rows": [...], "plan": kind, "row_overhead": r, "ms": t}; the
+        class table is also stored under "batch-<class>" keys."""
+        keys = [class_of(s.nx, s.ny, {"storage": s.params.storage, "collision": s.params.collision,
+                                      "equilibrium": s.params.equilibrium}) for s in sims]
+        rows = [0] * len(sims)
+
+        def timed(member_rows, kind=L.LBM_PLAN_AUTO, ovh=None):
+            b = L.Batch(sims, row_overhead=ovh, plan=kind, member_plan_rows=member_rows)
+            try:
+                return _event_ms(lambda n: b.step(n, use_graph=False), steps)
+            finally:
+                b.close()
+
+        best = timed(rows)
+        weight = {}
+        for s, k in zip(sims, keys):
+            weight[k] = weight.get(k, 0) + s.nx * s.ny
+        chosen = {}
+        for k in sorted(weight, key=weight.get, reverse=True):
+            pick = 0
+            for r in self.candidates:
+                if r == 8:
+                    continue   # the default (0 = 8) is the incumbent
+                trial = [r if kk == k else v for kk, v in zip(keys, rows)]
+                t = timed(trial)
+                if t < best * (1.0 - gain):
+                    best, pick = t, r
+            rows = [pick if kk == k else v for kk, v in zip(keys, rows)]
+            chosen[k] = pick if pick else 8
+            self.table["batch-" + k] = {"kernel": L.LBM_KERNEL_FUSED, "plan_rows": chosen[k]}
+        (kind, ovh), timings = tune_plan(sims, steps=steps, member_plan_rows=rows)
+        return {"classes": chosen, "member_plan_rows": rows, "plan": kind, "row_overhead": ovh,
+                "ms": timings[(kind, ovh)]}
 
     def params_for(self, nx: int, ny: int, batched: bool, **params) -> dict:
         """`params` with the tuned kernel and plan_rows of this size class (the
@@ -156,20 +179,22 @@ class Autotuner:
         return out
 
 
-def tune_row_overhead(sims, candidates=ROW_OVERHEAD_CANDIDATES, steps: int = 20) -> tuple[float, dict]:
-    """Planner cost of a strip row beyond its busy warps, timed on the batch itself.
+def tune_plan(sims, candidates=PLAN_OPTION_CANDIDATES, steps: int = 20,
+              member_plan_rows=None) -> tuple[tuple[int, float], dict]:
+    """Work plan of a batch, timed on the batch itself.
 
-    The balanced plan shares the strip rows of all members among the resident
-    blocks by cost; how much a narrow strip's row costs relative to a full one
-    depends on the mix of lattice widths, so each candidate is timed on the
-    whole batch (direct launches on torch's current stream).  The members'
-    states advance by (steps + warm-up) x len(candidates) steps: re-initialise
-    them afterwards.  Returns (best, {candidate: ms per step})."""
+    Each candidate (plan kind, row overhead) plans the strip rows of all members
+    differently; which is fastest depends on the mix of lattice sizes (how many
+    128-column strips there are per resident block, how narrow their last strips
+    are), so each is timed on the whole batch with direct launches on torch's
+    current stream.  The members' states advance by (steps + warm-up) x
+    len(candidates) steps: re-initialise them afterwards.  Returns
+    (best (kind, overhead), {(kind, overhead): ms per step})."""
     timings = {}
-    for c in candidates:
-        b = L.Batch(sims, row_overhead=float(c))
+    for kind, ovh in candidates:
+        b = L.Batch(sims, row_overhead=float(ovh), plan=int(kind), member_plan_rows=member_plan_rows)
         try:
-            timings[float(c)] = _event_ms(lambda n: b.step(n, use_graph=False), steps)
+            timings[(int(kind), float(ovh))] = _event_ms(lambda n: b.step(n, use_graph=False), steps)
         finally:
             b.close()
     best = min(timings, key=timings.get)

@@ -159,6 +159,7 @@ lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
     if (p->storage < 0 || p->storage > 2) { set_err(err, "unknown storage"); return LBM_EINVAL; }
     if (p->kernel < 0 || p->kernel > 2) { set_err(err, "unknown kernel"); return LBM_EINVAL; }
     if (p->plan_rows < 0 || p->plan_rows > (1 << 20)) { set_err(err, "plan_rows out of range"); return LBM_EINVAL; }
+    if (p->plan < LBM_PLAN_AUTO || p->plan > LBM_PLAN_SPLIT) { set_err(err, "unknown plan kind"); return LBM_EINVAL; }
     if (p->bc_x == LBM_BC_INOUT && !(p->p_out > 0.0)) {
         set_err(err, "inlet/outlet needs p_out > 0");
         return LBM_EINVAL;
@@ -373,6 +374,74 @@ Plan fixed_plan(const std::vector<StripRef> &strips, int rows) {
         }
     P.blocks = (int)P.items.size();
     return P;
+}
+
+// Split plan: every block gets exactly one segment (a block that starts a
+// second segment pays a second prologue and a second wait for its first row
+// loads, which costs more than it balances).  Each strip is cut into k_s nearly
+// equal pieces, with the k_s chosen so that the costliest piece is as cheap as
+// possible while sum k_s <= max_blocks and no piece is shorter than its strip's
+// min_piece.  Falls back to the balanced plan when there are more strips than
+// blocks.
+Plan split_plan(const std::vector<StripRef> &strips, int max_blocks, double row_overhead) {
+    if ((int)strips.size() > max_blocks || strips.empty()) return balanced_plan(strips, max_blocks, row_overhead);
+    const int n = (int)strips.size();
+    std::vector<double> cost(n);
+    std::vector<int> kmax(n);
+    for (int i = 0; i < n; i++) {
+        const auto &s = strips[i];
+        cost[i] = (double)s.ny * ((s.w + 31) / 32 + row_overhead);
+        kmax[i] = std::max(1, s.ny / std::max(1, s.min_piece));
+    }
+    auto pieces = [&](double C, std::vector<int> *k) {
+        long long tot = 0;
+        for (int i = 0; i < n; i++) {
+            // clamp in floating point: cost / C overflows an int as C -> 0
+            const double q = C > 0.0 ? std::ceil(cost[i] / C - 1e-9) : (double)kmax[i];
+            const int ki = q >= (double)kmax[i] ? kmax[i] : std::max(1, (int)q);
+            tot += ki;
+            if (k) (*k)[i] = ki;
+        }
+        return tot;
+    };
+    double lo = 0.0, hi = 0.0;
+    for (double c : cost) hi = std::max(hi, c);
+    if (pieces(hi, nullptr) > max_blocks) return balanced_plan(strips, max_blocks, row_overhead);
+    for (int it = 0; it < 60; it++) {   // smallest piece cost whose piece count fits
+        const double mid = 0.5 * (lo + hi);
+        if (pieces(mid, nullptr) <= max_blocks) hi = mid;
+        else lo = mid;
+    }
+    std::vector<int> k(n);
+    pieces(hi, &k);
+    Plan P;
+    P.off.push_back(0);
+    for (int i = 0; i < n; i++) {
+        const auto &s = strips[i];
+        const int base = s.ny / k[i], extra = s.ny % k[i];
+        int y = 0;
+        for (int j = 0; j < k[i]; j++) {
+            const int rows = base + (j < extra ? 1 : 0);
+            WorkItem it{};
+            it.sim = s.sim;
+            it.x0 = s.x0;
+            it.w = s.w;
+            it.ya = y;
+            it.yb = y + rows;
+            y += rows;
+            P.items.push_back(it);
+            P.off.push_back((int)P.items.size());
+        }
+    }
+    P.blocks = (int)P.items.size();
+    return P;
+}
+
+// Work plan of the given kind (lbm_plan_kind) over the strips.
+Plan make_plan(const std::vector<StripRef> &strips, int kind, int rows_per_item, int max_blocks, double row_overhead) {
+    if (rows_per_item > 0) return fixed_plan(strips, rows_per_item);
+    if (kind == LBM_PLAN_BALANCED) return balanced_plan(strips, max_blocks, row_overhead);
+    return split_plan(strips, max_blocks, row_overhead);
 }
 
 template <typename T, int CV>
@@ -651,7 +720,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
     {
         std::vector<StripRef> strips;
         strips_of(strips, 0, nx, ny, p->plan_rows);
-        Plan P = balanced_plan(strips, resident_blocks(p->storage, variant_of(p)), DEFAULT_ROW_OVERHEAD);
+        Plan P = make_plan(strips, p->plan, 0, resident_blocks(p->storage, variant_of(p)), DEFAULT_ROW_OVERHEAD);
         s->n_items = (int)P.items.size();
         s->n_blocks = P.blocks;
         if (cudaMalloc(&s->d_items, P.items.size() * sizeof(WorkItem)) != cudaSuccess ||
@@ -975,14 +1044,58 @@ lbm_status lbm_batch_create(lbm_sim *const *sims, int n, int rows_per_item, lbm_
     lbm_batch_opts o{};
     o.rows_per_item = rows_per_item;
     o.row_overhead = -1.0f;
+    o.plan = LBM_PLAN_AUTO;
+    o.member_plan_rows = nullptr;
     return lbm_batch_create_ex(sims, n, &o, out);
+}
+
+lbm_status lbm_plan_preview(const int *nx, const int *ny, const int *plan_rows, int n, const lbm_batch_opts *opts,
+                            int max_blocks, int *n_items, int *n_blocks, int *items, int capacity) {
+    if (!nx || !ny || n <= 0 || !opts || max_blocks <= 0 || !n_items || !n_blocks || capacity < 0 ||
+        (capacity > 0 && !items))
+        return LBM_EINVAL;
+    if (opts->rows_per_item < 0 || !(opts->row_overhead <= 64.0f) || opts->plan < LBM_PLAN_AUTO ||
+        opts->plan > LBM_PLAN_SPLIT)
+        return LBM_EINVAL;
+    std::vector<StripRef> strips;
+    for (int i = 0; i < n; i++) {
+        const int pr = opts->member_plan_rows ? opts->member_plan_rows[i] : (plan_rows ? plan_rows[i] : 0);
+        if (nx[i] < 1 || ny[i] < 1 || pr < 0 || pr > (1 << 20)) return LBM_EINVAL;
+        strips_of(strips, i, nx[i], ny[i], pr);
+    }
+    const double ovh = opts->row_overhead < 0.0f ? DEFAULT_ROW_OVERHEAD : (double)opts->row_overhead;
+    const Plan P = make_plan(strips, opts->plan, opts->rows_per_item, max_blocks, ovh);
+    *n_items = (int)P.items.size();
+    *n_blocks = P.blocks;
+    for (int b = 0; b < P.blocks; b++)
+        for (int q = P.off[b]; q < P.off[b + 1]; q++)
+            if (q < capacity) {
+                const WorkItem &it = P.items[q];
+                int *o = items + 6 * q;
+                o[0] = it.sim;
+                o[1] = it.x0;
+                o[2] = it.w;
+                o[3] = it.ya;
+                o[4] = it.yb;
+                o[5] = b;
+            }
+    return LBM_OK;
 }
 
 lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts *opts, lbm_batch **out) {
     if (!out || !sims || n <= 0 || !opts) { set_err(g_create_err, "empty batch or no options"); return LBM_EINVAL; }
     const int rows_per_item = opts->rows_per_item;
     const double row_overhead = opts->row_overhead < 0.0f ? DEFAULT_ROW_OVERHEAD : (double)opts->row_overhead;
-    if (rows_per_item < 0 || !(row_overhead <= 64.0)) { set_err(g_create_err, "batch options out of range"); return LBM_EINVAL; }
+    if (rows_per_item < 0 || !(row_overhead <= 64.0) || opts->plan < LBM_PLAN_AUTO || opts->plan > LBM_PLAN_SPLIT) {
+        set_err(g_create_err, "batch options out of range");
+        return LBM_EINVAL;
+    }
+    if (opts->member_plan_rows)
+        for (int i = 0; i < n; i++)
+            if (opts->member_plan_rows[i] < 0 || opts->member_plan_rows[i] > (1 << 20)) {
+                set_err(g_create_err, "member_plan_rows[%d] out of range", i);
+                return LBM_EINVAL;
+            }
     *out = nullptr;
     long long strip_rows = 0;
     for (int i = 0; i < n; i++) {
@@ -1010,10 +1123,10 @@ lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts
             std::vector<StripRef> strips;
             for (int i = 0; i < n; i++)
                 if (sims[i]->p.storage == st && sims[i]->h.variant == cv)
-                    strips_of(strips, i, sims[i]->nx, sims[i]->ny, sims[i]->p.plan_rows);
+                    strips_of(strips, i, sims[i]->nx, sims[i]->ny,
+                              opts->member_plan_rows ? opts->member_plan_rows[i] : sims[i]->p.plan_rows);
             if (strips.empty()) continue;
-            Plan P = rows_per_item > 0 ? fixed_plan(strips, rows_per_item)
-                                       : balanced_plan(strips, resident_blocks(st, cv), row_overhead);
+            Plan P = make_plan(strips, opts->plan, rows_per_item, resident_blocks(st, cv), row_overhead);
             lbm_batch::Group g{st, cv, (int)items.size(), (int)offs.size(), P.blocks};
             for (int &o : P.off) o += g.item0;
             items.insert(items.end(), P.items.begin(), P.items.end());

@@ -37,14 +37,19 @@ ABI_SYMBOLS = (
     "lbm_init_slug", "lbm_init_fields", "lbm_init_populations", "lbm_step", "lbm_set_stop",
     "lbm_synchronize", "lbm_time", "lbm_read_fields", "lbm_read_populations",
     "lbm_diagnostics", "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_last_error",
-    "lbm_destroy", "lbm_batch_create", "lbm_batch_create_ex", "lbm_batch_step", "lbm_batch_items",
+    "lbm_destroy", "lbm_batch_create", "lbm_batch_create_ex", "lbm_plan_preview", "lbm_batch_step",
+    "lbm_batch_items",
     "lbm_batch_destroy",
     "lbm_step_noalloc",
 )
 
 
+LBM_PLAN_AUTO, LBM_PLAN_BALANCED, LBM_PLAN_SPLIT = 0, 1, 2
+
+
 class lbm_batch_opts(ctypes.Structure):
-    _fields_ = [("rows_per_item", ctypes.c_int), ("row_overhead", ctypes.c_float)]
+    _fields_ = [("rows_per_item", ctypes.c_int), ("row_overhead", ctypes.c_float), ("plan", ctypes.c_int),
+                ("member_plan_rows", ctypes.POINTER(ctypes.c_int))]
 
 
 class lbm_params(ctypes.Structure):
@@ -59,7 +64,7 @@ class lbm_params(ctypes.Structure):
         ("u_in_r", ctypes.c_double), ("u_in_b", ctypes.c_double), ("p_out", ctypes.c_double),
         ("inlet_mode", ctypes.c_int), ("inlet_period_r", ctypes.c_int),
         ("inlet_period_b", ctypes.c_int), ("inlet_layer", ctypes.c_int),
-        ("kernel", ctypes.c_int), ("plan_rows", ctypes.c_int),
+        ("kernel", ctypes.c_int), ("plan_rows", ctypes.c_int), ("plan", ctypes.c_int),
     ]
 
 
@@ -133,6 +138,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbm_step_noalloc.argtypes = [pp, i, i, vp, st, ctypes.c_longlong, l, vp]
     L.lbm_batch_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(vp)]
     L.lbm_batch_create_ex.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(lbm_batch_opts), ctypes.POINTER(vp)]
+    L.lbm_plan_preview.argtypes = [ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), i,
+                                   ctypes.POINTER(lbm_batch_opts), i, ctypes.POINTER(i), ctypes.POINTER(i),
+                                   ctypes.POINTER(i), i]
     L.lbm_batch_step.argtypes = [vp, l, i]
     L.lbm_batch_items.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
@@ -266,15 +274,43 @@ def lbm_step_noalloc(p: lbm_params, nx: int, ny: int, state_ptr: int, nbytes: in
                                    ctypes.c_void_p(stream)))
 
 
-def lbm_batch_create(sims, rows_per_item: int = 0, row_overhead: float | None = None) -> int:
+def lbm_batch_create(sims, rows_per_item: int = 0, row_overhead: float | None = None,
+                     plan: int = LBM_PLAN_AUTO, member_plan_rows=None) -> int:
     arr = (ctypes.c_void_p * len(sims))(*sims)
     h = ctypes.c_void_p()
-    if row_overhead is None:
+    if row_overhead is None and plan == LBM_PLAN_AUTO and member_plan_rows is None:
         _check(load().lbm_batch_create(arr, len(sims), rows_per_item, ctypes.byref(h)))
     else:
-        opts = lbm_batch_opts(rows_per_item=rows_per_item, row_overhead=row_overhead)
+        rows = None
+        if member_plan_rows is not None:
+            if len(member_plan_rows) != len(sims):
+                raise ValueError("member_plan_rows needs one value per member")
+            rows = (ctypes.c_int * len(sims))(*[int(r) for r in member_plan_rows])
+        opts = lbm_batch_opts(rows_per_item=rows_per_item,
+                              row_overhead=-1.0 if row_overhead is None else row_overhead, plan=plan,
+                              member_plan_rows=rows)
         _check(load().lbm_batch_create_ex(arr, len(sims), ctypes.byref(opts), ctypes.byref(h)))
     return h.value
+
+
+def lbm_plan_preview(sizes, max_blocks: int, plan: int = LBM_PLAN_AUTO, row_overhead: float | None = None,
+                     rows_per_item: int = 0, plan_rows=None) -> tuple[int, np.ndarray]:
+    """Host-only preview of a batch's work plan: (blocks, items) with items an
+    (n_items, 6) int array of member, x0, width, first row, end row, block."""
+    n = len(sizes)
+    nx = (ctypes.c_int * n)(*[int(a) for a, _ in sizes])
+    ny = (ctypes.c_int * n)(*[int(b) for _, b in sizes])
+    pr = None if plan_rows is None else (ctypes.c_int * n)(*[int(r) for r in plan_rows])
+    opts = lbm_batch_opts(rows_per_item=rows_per_item, row_overhead=-1.0 if row_overhead is None else row_overhead,
+                          plan=plan)
+    ni, nb = ctypes.c_int(), ctypes.c_int()
+    lib = load()
+    _check(lib.lbm_plan_preview(nx, ny, pr, n, ctypes.byref(opts), max_blocks, ctypes.byref(ni), ctypes.byref(nb),
+                                None, 0))
+    buf = (ctypes.c_int * (6 * ni.value))()
+    _check(lib.lbm_plan_preview(nx, ny, pr, n, ctypes.byref(opts), max_blocks, ctypes.byref(ni), ctypes.byref(nb),
+                                buf, ni.value))
+    return nb.value, np.array(buf, dtype=np.int64).reshape(ni.value, 6)
 
 
 def lbm_batch_step(batch: int, n: int, use_graph: bool = True, sim_for_errors=None):
@@ -387,11 +423,14 @@ class Simulation:
 class Batch:
     """Several simulations advanced together, one launch per step."""
 
-    def __init__(self, sims, rows_per_item: int = 0, row_overhead: float | None = None):
-        """rows_per_item > 0: fixed plan; row_overhead: planner's fixed cost of a
-        strip row in busy warps (None: library default)."""
+    def __init__(self, sims, rows_per_item: int = 0, row_overhead: float | None = None,
+                 plan: int = LBM_PLAN_AUTO, member_plan_rows=None):
+        """rows_per_item > 0: fixed plan; otherwise `plan` (LBM_PLAN_*) with
+        row_overhead, the planner's fixed cost of a strip row in busy warps
+        (None: library default), and optionally one plan_rows per member in
+        place of the members' own."""
         self.sims = list(sims)
-        self.h = lbm_batch_create([s.h for s in self.sims], rows_per_item, row_overhead)
+        self.h = lbm_batch_create([s.h for s in self.sims], rows_per_item, row_overhead, plan, member_plan_rows)
 
     @property
     def items(self) -> int:

@@ -62,6 +62,8 @@ def test_batch_options_are_checked_before_any_device_call():
     opts = L.lbm_batch_opts(rows_per_item=0, row_overhead=1.0)
     assert lib.lbm_batch_create_ex(arr, 0, ctypes.byref(opts), ctypes.byref(h)) == L.LBM_EINVAL
     assert lib.lbm_batch_create_ex(arr, 1, None, ctypes.byref(h)) == L.LBM_EINVAL
+    bad = L.lbm_batch_opts(rows_per_item=0, row_overhead=1.0, plan=7)
+    assert lib.lbm_batch_create_ex(arr, 1, ctypes.byref(bad), ctypes.byref(h)) == L.LBM_EINVAL
     assert h.value is None
 
 

@@ -40,21 +40,28 @@ def test_plan_rows_never_changes_results(storage):
 
 
 def test_tuned_batch_equals_alone():
-    """A batch whose members carry the tuned plan_rows of their size classes gives
-    each member the state it reaches alone with the default plan."""
+    """A batch planned with what the tuner picked (per class plan_rows, plan kind,
+    row cost) gives each member the state it reaches alone with the default plan."""
     specs = [(96, 64), (300, 200), (128, 512), (300, 210)]
-    members = [(nx, ny, dict(gamma=10.0, sigma=0.005, storage=1)) for nx, ny in specs]
-    tuner = A.Autotuner(steps=6, candidates=(8, 32))
-    table = tuner.tune_batch(members)
-    assert len(table) == 3   # 300x200 and 300x210 share a class
-    sims = []
-    for nx, ny, kw in members:
-        s = L.Simulation(nx, ny, **tuner.params_for(nx, ny, True, **kw))
+    kw = dict(gamma=10.0, sigma=0.005, storage=1)
+
+    def start(nx, ny):
+        s = L.Simulation(nx, ny, torch_memory=True, **kw)
         s.init_fields(*W.bubble_fields(nx, ny, nx / 2, ny / 2, ny / 4, 10.0))
-        sims.append(s)
-    b = L.Batch(sims)
+        return s
+
+    sims = [start(nx, ny) for nx, ny in specs]
+    tuner = A.Autotuner(candidates=(8, 32))
+    got = tuner.tune_batch(sims, steps=4)
+    assert set(got["classes"]) == {A.class_of(nx, ny, {"storage": 1}) for nx, ny in specs}
+    assert len(got["classes"]) == 3   # 300x200 and 300x210 share a class
+    assert all(r in (0, 32) for r in got["member_plan_rows"])
+    for s in sims:
+        s.close()
+    sims = [start(nx, ny) for nx, ny in specs]
+    b = L.Batch(sims, row_overhead=got["row_overhead"], plan=got["plan"], member_plan_rows=got["member_plan_rows"])
     b.step(25, use_graph=True)
-    for s, (nx, ny, kw) in zip(sims, members):
+    for s, (nx, ny) in zip(sims, specs):
         s.synchronize()
         assert s.save_state() == _state(nx, ny, 25, **kw)
     b.close()
@@ -62,9 +69,9 @@ def test_tuned_batch_equals_alone():
         s.close()
 
 
-def test_row_overhead_never_changes_results():
-    """The planner's row cost only moves rows between thread blocks: batches
-    planned with every candidate cost reach bit-identical states, and the tuner
+def test_plan_options_never_change_results():
+    """Plan kind and row cost only move rows between thread blocks: batches
+    planned with every candidate reach bit-identical states, and the tuner
     returns one of the candidates."""
     specs = [(96, 64), (160, 200), (300, 90), (32, 128)]
 
@@ -77,9 +84,9 @@ def test_row_overhead_never_changes_results():
         return out
 
     ref = None
-    for c in A.ROW_OVERHEAD_CANDIDATES:
+    for kind, c in A.PLAN_OPTION_CANDIDATES + ((L.LBM_PLAN_AUTO, -1.0),):
         sims = members()
-        b = L.Batch(sims, row_overhead=c)
+        b = L.Batch(sims, row_overhead=c, plan=kind)
         b.step(17, use_graph=False)
         sims[0].synchronize()
         states = [s.save_state() for s in sims]
@@ -90,7 +97,7 @@ def test_row_overhead_never_changes_results():
             ref = states
         assert states == ref
     sims = members()
-    best, timings = A.tune_row_overhead(sims, steps=4)
-    assert best in A.ROW_OVERHEAD_CANDIDATES and set(timings) == set(A.ROW_OVERHEAD_CANDIDATES)
+    best, timings = A.tune_plan(sims, steps=4)
+    assert best in A.PLAN_OPTION_CANDIDATES and set(timings) == set(A.PLAN_OPTION_CANDIDATES)
     for s in sims:
         s.close()
