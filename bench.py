@@ -37,7 +37,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic of one k_step_fused launch on this workload from an ncu capture
 # (profiles/k_step_fused_laplace_sweep_40x256.md), valid only for the kernel
 # sources with this hash; reported as null otherwise.
-NCU_TRAFFIC = {"sources_sha": "78947a3b6ff155d5", "bytes_per_launch": 258693120 + 163757568}
+NCU_TRAFFIC = {"sources_sha": "b29152c4327a3eac", "bytes_per_launch": 222832640 + 155406848}
 
 
 def kernel_sources_sha() -> str:
