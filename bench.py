@@ -30,8 +30,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# per node update: 2 FP32 densities + 16 deviations, read and written
-BYTES_PER_UPDATE = {0: 144, 1: 80, 2: 80}
+# per node update, read and written: 2 FP32 densities + 16 FP32 deviations, or 5 FP32
+# node scalars (densities and the split-form scalars) + 16 16-bit deviation residuals
+BYTES_PER_UPDATE = {0: 144, 1: 104, 2: 104}
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic of one k_step_fused launch on this workload from an ncu capture

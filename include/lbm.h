@@ -57,8 +57,16 @@ typedef enum {
 
 typedef enum { LBM_BGK = 0, LBM_MRT = 1 } lbm_collision;
 typedef enum { LBM_EQ_STD = 0, LBM_EQ_HERMITE = 1 } lbm_equilibrium;
-/* Population storage: FP32, or 16-bit deviations from the rest state with FP32
- * arithmetic. */
+/* Population storage (arithmetic is FP32 in every case).  The state holds per
+ * node the colour densities rho_r, rho_b (FP32) and the deviations
+ * d^k_i = N^k_i - phi^k_i rho_k of the post-collision populations from the rest
+ * state of the node's own colour densities (i = 1..8).
+ *   F32     deviations in FP32: 144 bytes read + written per node update.
+ *   F16DEV  deviations in FP16 and BF16DEV in BF16, in a split form.  The
+ *   BF16DEV recolouring shift and flux that dominate d^k_i at an interface
+ *           (Eq. (eq:recoloringOperator)) are rebuilt from three FP32 node
+ *           scalars (rho_r rho_b / rho and the flux vector), and only the small
+ *           colour-blind remainder is rounded to 16 bits: 104 bytes per update. */
 typedef enum { LBM_F32 = 0, LBM_F16DEV = 1, LBM_BF16DEV = 2 } lbm_storage;
 /* bc_x: PERIODIC or INOUT; bc_y: PERIODIC or WALL. */
 typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_WALL = 1, LBM_BC_INOUT = 2 } lbm_bc;

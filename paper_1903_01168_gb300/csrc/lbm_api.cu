@@ -176,8 +176,12 @@ int pitch_dev(int nx, int storage) {
     return (nx + 2 * GHOST + align - 1) / align * align;
 }
 
-size_t rho_region_bytes(int nx, int ny) {
-    const size_t b = 2ull * 2ull * (size_t)ny * pitch_rho(nx) * 4ull;
+// FP32 node planes per row: rho_r, rho_b, plus the split-form scalars m, G_x, G_y
+// for 16-bit deviations.
+int scalar_planes(int storage) { return storage == ST_F32 ? 2 : 5; }
+
+size_t rho_region_bytes(int nx, int ny, int storage) {
+    const size_t b = 2ull * (size_t)scalar_planes(storage) * (size_t)ny * pitch_rho(nx) * 4ull;
     return (b + 255) / 256 * 256;
 }
 
@@ -197,7 +201,7 @@ void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     h.pitch_r = pitch_rho(nx);
     h.pitch_d = pitch_dev(nx, p->storage);
     h.rho_plane = h.pitch_r;
-    h.rho_row = 2LL * h.pitch_r;
+    h.rho_row = (long long)scalar_planes(p->storage) * h.pitch_r;
     h.rho_buf = (long long)ny * h.rho_row;
     h.dev_plane = h.pitch_d;
     h.dev_row = 16LL * h.pitch_d;
@@ -223,6 +227,7 @@ void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     for (int c = 0; c < 3; c++) {
         f.phi_r[c] = (float)ar[c];
         f.phi_b[c] = (float)ab[c];
+        f.dphi[c] = f.phi_b[c] - f.phi_r[c];
     }
     f.omega_r = (float)wr;
     f.omega_b = (float)wb;
@@ -261,9 +266,10 @@ lbm_status encode_tmap(lbm_sim *s) {
     // rows of planes over both buffers: [2][ny][planes] -> one 2D row index
     cuuint32_t estr[2] = {1, 1};
     {
-        cuuint64_t dims[2] = {(cuuint64_t)s->h.pitch_r, (cuuint64_t)s->ny * 2 * 2};
+        const cuuint32_t ns = (cuuint32_t)scalar_planes(s->p.storage);
+        cuuint64_t dims[2] = {(cuuint64_t)s->h.pitch_r, (cuuint64_t)s->ny * 2 * ns};
         cuuint64_t strides[1] = {(cuuint64_t)s->h.pitch_r * 4};
-        cuuint32_t box[2] = {box_w, 2};
+        cuuint32_t box[2] = {box_w, ns};
         CUresult r = enc(&s->h.tmap_rho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s->h.rho, dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -711,7 +717,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         s->own_stream = true;
     }
     s->h.rho = reinterpret_cast<float *>(s->pop);
-    s->h.dev = static_cast<char *>(s->pop) + rho_region_bytes(nx, ny);
+    s->h.dev = static_cast<char *>(s->pop) + rho_region_bytes(nx, ny, p->storage);
     if (encode_tmap(s) != LBM_OK) return fail(LBM_ECUDA);
     if (cudaMalloc(&s->d_desc, sizeof(SimDesc)) != cudaSuccess || cudaMalloc(&s->d_err, sizeof(int)) != cudaSuccess) {
         set_err(s->err, "cudaMalloc of descriptor failed");
@@ -763,7 +769,7 @@ lbm_status host_validate(int nx, int ny, const lbm_params *p, char *err) { retur
 void host_fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p, void *state) {
     fill_desc(h, nx, ny, p);
     h.rho = reinterpret_cast<float *>(state);
-    h.dev = static_cast<char *>(state) + rho_region_bytes(nx, ny);
+    h.dev = static_cast<char *>(state) + rho_region_bytes(nx, ny, p->storage);
 }
 
 void host_set_global_error(const char *msg) { snprintf(g_create_err, sizeof(g_create_err), "%s", msg); }
@@ -790,7 +796,7 @@ lbm_status lbm_default_params(lbm_params *p) {
 size_t lbm_bytes_required(int nx, int ny, const lbm_params *p) {
     char tmp[256];
     if (validate(nx, ny, p, tmp) != LBM_OK) return 0;
-    return rho_region_bytes(nx, ny) + dev_region_bytes(nx, ny, p->storage);
+    return rho_region_bytes(nx, ny, p->storage) + dev_region_bytes(nx, ny, p->storage);
 }
 
 lbm_status lbm_create(int nx, int ny, const lbm_params *p, lbm_sim **out) {

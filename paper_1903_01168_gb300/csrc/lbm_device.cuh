@@ -34,8 +34,21 @@ enum : int { ERR_TIMEOUT = 1, ERR_BADITEM = 2, ERR_ALIGN = 4 };
 // deviation d^k_0 = -sum_{i>=1} d^k_i is implied, so every node's deviations
 // sum to zero exactly, a colour that is absent is an exact zero, and all
 // quantities the step manipulates are small where a phase is at rest.
-//   rho planes: [2 buffers][ny][2 colours][pitch_r]          float
+//   rho planes: [2 buffers][ny][NS][pitch_r]                 float
 //   dev planes: [2 buffers][ny][16 = colour * 8 + (i - 1)][pitch_d]   T
+// NS = 2 (rho_r, rho_b) with FP32 deviations.  With 16-bit deviations NS = 5:
+// rho_r, rho_b and the node scalars m, G_x, G_y of the split form below.
+//
+// Split form (16-bit storage).  After recolouring (Eq. (eq:recoloringOperator))
+// a node's deviations are
+//   d^r_i =  m dphi_c + t_i + (rho_r / rho) E_i,
+//   d^b_i = -m dphi_c - t_i + (rho_b / rho) E_i,
+// with m = rho_r rho_b / rho, dphi_c = phi^b_c - phi^r_c (c = |c_i|^2),
+// t_i = (c_i . G) / |c_i| (rho_r phi^r_c + rho_b phi^b_c), G = beta m / rho F / |F|,
+// and E_i the colour-blind non-rest part.  At an interface the first two terms
+// are O(m) while E_i is small, so only the residuals r^k_i = d^k_i -+ (m dphi_c
+// + t_i) are rounded to 16 bits and m, G stay FP32.  Any state is
+// representable: the initial state stores m = G = 0 and r = d.
 // i.e. the planes of one lattice row lie next to each other, so that reading
 // or writing a row of a strip touches one contiguous stretch of memory per
 // array (a planar [plane][ny] layout spreads it over 18 distant pages and
@@ -50,6 +63,7 @@ struct Phys {
     float inv_gamma;           // 1 / rho_r^0
     float gx, gy;              // body acceleration
     float phi_r[3], phi_b[3];  // rest weights phi^k by |c|^2 = 0, 1, 2
+    float dphi[3];             // phi_b - phi_r by |c|^2
     float omega_r, omega_b, chi, eta, kappa, lam, nu, delta;
     float a_coef;              // A = a_coef * omega_eff, a_coef = 9 sigma / 4
     float beta, mrt_lambda, c7;
@@ -116,6 +130,36 @@ template <> struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 enc(float v) { return __float2bfloat16_rn(v); }
 };
 
+// 16-bit deviations are stored in the split form; FP32 ones directly.
+template <typename T> struct SplitStore { static constexpr bool value = sizeof(T) == 2; };
+template <typename T> struct ScalarPlanes { static constexpr int value = SplitStore<T>::value ? 5 : 2; };
+
+// Constants of the split form that a loader needs (by |c|^2 = 1, 2).
+struct SplitC {
+    float phr1, phr2, phb1, phb2, dph1, dph2;
+};
+
+__device__ __forceinline__ SplitC split_consts(const Phys &p) {
+    return SplitC{p.phi_r[1], p.phi_r[2], p.phi_b[1], p.phi_b[2], p.dphi[1], p.dphi[2]};
+}
+
+// Shift of the split form for direction i (added to red, subtracted from blue):
+// m dphi_c + (c_i . G) / |c_i| (rho_r phi^r_c + rho_b phi^b_c).  Every operation is
+// rounded explicitly, so that a node's deviation decodes to the same value
+// wherever it is read (the puller and the node itself), which keeps the colour
+// mass exchanged between nodes balanced.
+__device__ __forceinline__ float split_shift(const SplitC &q, int i, float rr, float rb, float m, float gx,
+                                             float gy) {
+    const bool axis = C2(i) == 1;
+    const float rest = __fmaf_rn(rr, axis ? q.phr1 : q.phr2, __fmul_rn(rb, axis ? q.phb1 : q.phb2));
+    float gc;
+    if (CY(i) == 0) gc = CX(i) > 0 ? gx : -gx;
+    else if (CX(i) == 0) gc = CY(i) > 0 ? gy : -gy;
+    else gc = __fadd_rn(CX(i) > 0 ? gx : -gx, CY(i) > 0 ? gy : -gy);
+    const float inv_c = axis ? 1.0f : 0.70710678118654752f;
+    return __fadd_rn(__fmul_rn(m, axis ? q.dph1 : q.dph2), __fmul_rn(__fmul_rn(gc, inv_c), rest));
+}
+
 __device__ __forceinline__ float phi_k(const Phys &p, int k, int c2) { return k == 0 ? p.phi_r[c2] : p.phi_b[c2]; }
 
 // Where node (x, y)'s post-collision state goes in buffer b: row pointers of
@@ -141,9 +185,14 @@ struct NodeStore {
     }
 
     __device__ __forceinline__ void store_at(int off, float rr, float rb, const float (&dr)[9],
-                                             const float (&db)[9]) const {
+                                             const float (&db)[9], float m, float gx, float gy) const {
         rho[off] = rr;
         rho[rho_plane + off] = rb;
+        if (SplitStore<T>::value) {
+            rho[2 * rho_plane + off] = m;
+            rho[3 * rho_plane + off] = gx;
+            rho[4 * rho_plane + off] = gy;
+        }
 #pragma unroll
         for (int i = 1; i < 9; i++) {
             dev[(i - 1) * dev_plane + off] = Codec<T>::enc(dr[i]);
@@ -151,10 +200,19 @@ struct NodeStore {
         }
     }
 
+    // Post-collision state: with 16-bit storage dr, db are the split-form
+    // residuals and (m, gx, gy) its node scalars; with FP32 storage dr, db are
+    // the deviations and the scalars are ignored.
+    __device__ __forceinline__ void put(float rr, float rb, const float (&dr)[9], const float (&db)[9], float m,
+                                        float gx, float gy) const {
+        store_at(0, rr, rb, dr, db, m, gx, gy);
+        if (mirror_r) store_at(mirror_r, rr, rb, dr, db, m, gx, gy);
+        if (mirror_l) store_at(mirror_l, rr, rb, dr, db, m, gx, gy);
+    }
+
+    // Any state given by its deviations (split form with m = G = 0).
     __device__ __forceinline__ void store(float rr, float rb, const float (&dr)[9], const float (&db)[9]) const {
-        store_at(0, rr, rb, dr, db);
-        if (mirror_r) store_at(mirror_r, rr, rb, dr, db);
-        if (mirror_l) store_at(mirror_l, rr, rb, dr, db);
+        put(rr, rb, dr, db, 0.0f, 0.0f, 0.0f);
     }
 };
 
@@ -232,12 +290,72 @@ struct Pulled {
 // NOT wrapped (the loader wraps periodic rows); y itself may lie one row
 // outside [0, ny) on a periodic lattice.  With have_rho the node's new colour
 // densities are already known (rr_new, rb_new) and are not recomputed.
+// pull_node for the split form (16-bit storage), away from open columns.  The
+// loader gives the stored residual r^k_i and the shift h_i of the split form
+// (d^r_i = r^r_i + h_i, d^b_i = r^b_i - h_i).  The shifts cancel in the colour-blind
+// parts e_i, and enter the colour densities only through one sum per node,
+//   sum_i h_i(source of i) - sum_i h_i(x),
+// where the node's own sum is 4 m (dphi_1 + dphi_2) (the flux parts cancel in
+// opposite pairs).
+template <class Loader>
+__device__ __forceinline__ void pull_node_split(const Phys &p, const Loader &ld, int x, int y, bool have_rho,
+                                                float rr_new, float rb_new, Pulled &P) {
+    const bool wall_y = p.bc_y == BC_WALL;
+    const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
+    float s[2][9], rs[2][9], own_rho[2];
+    own_rho[0] = ld.rho(0, x, y);
+    own_rho[1] = ld.rho(1, x, y);
+    float hsum = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+        const int xs = bounce ? x : x - CX(i), ys = bounce ? y : y - CY(i);
+        const int ii = bounce ? OPP(i) : i;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            s[k][i] = bounce ? own_rho[k] : ld.rho(k, xs, ys);
+            rs[k][i] = ld.res(k, ii, xs, ys);
+        }
+        // evaluated for every node: skipping it where all densities are pure (where
+        // it is exactly zero) leaves the warps of a block unbalanced at the row barrier
+        hsum += ld.shift(ii, xs, ys);
+    }
+    float rnew[2];
+    if (have_rho) {
+        rnew[0] = rr_new;
+        rnew[1] = rb_new;
+    } else {
+        const float dh = hsum - ld.own_shift_sum(x, y);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int i = 1; i < 9; i++)
+                acc += phi_k(p, k, C2(i)) * (s[k][i] - own_rho[k]) + (rs[k][i] - ld.res(k, i, x, y));
+            rnew[k] = own_rho[k] + (k == 0 ? acc + dh : acc - dh);
+        }
+    }
+    P.rr = rnew[0];
+    P.rb = rnew[1];
+    float e0 = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; i++) {
+        P.e[i] = p.phi_r[C2(i)] * (s[0][i] - rnew[0]) + rs[0][i] + p.phi_b[C2(i)] * (s[1][i] - rnew[1]) + rs[1][i];
+        e0 += P.e[i];
+    }
+    P.e[0] = -e0;
+}
+
 template <bool HERMITE, class Loader>
 __device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x, int y, long long t,
                                           bool have_rho, float rr_new, float rb_new, Pulled &P) {
     const bool wall_y = p.bc_y == BC_WALL;
     const bool open_col = p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1);
     const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
+    if (Loader::SPLIT && !open_col) {
+        pull_node_split(p, ld, x, y, have_rho, rr_new, rb_new, P);
+        return;
+    }
     float s[2][9], dl[2][9], own_rho[2];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
@@ -326,6 +444,47 @@ __device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, in
     }
     const bool wall_y = p.bc_y == BC_WALL;
     const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
+    if (Loader::SPLIT) {
+        // split form: residual differences per colour, one shift sum for both
+        // (as in pull_node_split)
+        float n[2][9], acc[2], own[2];
+        float hsum = 0.0f;
+        own[0] = ld.rho(0, x, y);
+        own[1] = ld.rho(1, x, y);
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+            const int xs = bounce ? x : x - CX(i), ys = bounce ? y : y - CY(i);
+            const int ii = bounce ? OPP(i) : i;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const float sv = bounce ? own[k] : ld.rho(k, xs, ys);
+                n[k][i] = phi_k(p, k, C2(i)) * (sv - own[k]) + ld.res(k, ii, xs, ys);
+            }
+            hsum += ld.shift(ii, xs, ys);
+        }
+        const float dh = hsum - ld.own_shift_sum(x, y);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            float a = 0.0f;
+#pragma unroll
+            for (int i = 1; i < 9; i++) a += n[k][i] - ld.res(k, i, x, y);
+            acc[k] = own[k] + (k == 0 ? a + dh : a - dh);
+        }
+        rr = acc[0];
+        rb = acc[1];
+        if (NEED_J) {
+            // colour-blind momentum: the shifts cancel between the colours
+            float m[9];
+#pragma unroll
+            for (int i = 1; i < 9; i++) m[i] = n[0][i] + n[1][i];
+            jx = (m[1] - m[3]) + (m[5] - m[7]) + (m[8] - m[6]);
+            jy = (m[2] - m[4]) + (m[5] - m[7]) + (m[6] - m[8]);
+        } else {
+            jx = jy = 0.0f;
+        }
+        return;
+    }
     float n[2][9];   // n[k][i] = N^k_i - phi^k_i rho_k(x) for i >= 1 (small)
     float acc[2];
 #pragma unroll
@@ -424,9 +583,10 @@ __device__ __forceinline__ float omega_eff(const Phys &p, float psi) {
 // dQy = d_y(q u_y) with q = sum_k (1.8 alpha_k - 0.8) rho_k.  Outputs the
 // post-collision deviations dr[1..8], db[1..8] of the stored state (the colour
 // densities are unchanged by the step's collision part).
-template <int CV>
+template <int CV, bool SPLIT = false>
 __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, float psi, float Fx, float Fy,
-                                             float dQx, float dQy, float (&dr)[9], float (&db)[9]) {
+                                             float dQx, float dQy, float (&dr)[9], float (&db)[9], float &o_m,
+                                             float &o_gx, float &o_gy) {
     constexpr bool MRT = (CV & CV_MRT) != 0, HERMITE = (CV & CV_HERMITE) != 0;
     const float rr = P.rr, rb = P.rb;
     const float rho = rr + rb;
@@ -541,6 +701,8 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
     const float fr = rr * inv_rho, fb = rb * inv_rho;
     const float mix = rr * rb * inv_rho;
     const float F2 = Fx * Fx + Fy * Fy;
+    o_m = mix;
+    o_gx = o_gy = 0.0f;
     // per |c|^2 class: shift of the stored deviations
     const float sh1 = mix * (p.phi_b[1] - p.phi_r[1]), sh2 = mix * (p.phi_b[2] - p.phi_r[2]);
     if (F2 > 0.0f) {
@@ -551,6 +713,25 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
         const float A = p.a_coef * w;
         const float pa = A * invFn, pb = A * Fn;
         const float kk = p.beta * mix * inv_rho * invFn;   // beta rr rb / rho^2 / |F|
+        if (SPLIT) {
+            // only the residuals (rho_k / rho) E_i are stored; the shift and the
+            // recolouring flux are rebuilt from m and G = kk F (split_shift)
+            o_gx = kk * Fx;
+            o_gy = kk * Fy;
+#pragma unroll
+            for (int i : {1, 2, 5, 6}) {
+                const int j = OPP(i);
+                const float Fc = CX(i) * Fx + CY(i) * Fy;
+                const float pert = pa * WT(i) * Fc * Fc - pb * BP(i);
+                const float Ei = e[i] + pert, Ej = e[j] + pert;
+                dr[i] = fr * Ei;
+                dr[j] = fr * Ej;
+                db[i] = fb * Ei;
+                db[j] = fb * Ej;
+            }
+            dr[0] = db[0] = 0.0f;
+            return;
+        }
         // cos(phi_i) = c_i.F / (|c_i| |F|); rest_i = rr phi^r_i + rb phi^b_i
         const float k1 = kk * (rr * p.phi_r[1] + rb * p.phi_b[1]);
         const float k2 = kk * 0.70710678118654752f * (rr * p.phi_r[2] + rb * p.phi_b[2]);
@@ -566,6 +747,12 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
             dr[j] = sh + fr * Ej - term;
             db[i] = -sh + fb * Ei - term;
             db[j] = -sh + fb * Ej + term;
+        }
+    } else if (SPLIT) {
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            dr[i] = fr * e[i];
+            db[i] = fb * e[i];
         }
     } else {
 #pragma unroll

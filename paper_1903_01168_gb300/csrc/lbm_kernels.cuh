@@ -31,6 +31,7 @@ struct GlobalLoader {
     const T *dev0;       // &dev[b][0][0][0]
     long long rho_plane, dev_plane, rho_row, dev_row;
     int ny;
+    SplitC q;
     __device__ __forceinline__ GlobalLoader(const SimDesc &d, int b) {
         rho0 = d.rho + b * d.rho_buf + d.ghost;
         dev0 = reinterpret_cast<const T *>(d.dev) + b * d.dev_buf + d.ghost;
@@ -39,23 +40,42 @@ struct GlobalLoader {
         rho_row = d.rho_row;
         dev_row = d.dev_row;
         ny = d.ph.ny;
+        q = split_consts(d.ph);
     }
     __device__ __forceinline__ int wrap(int ys) const { return ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys); }
     __device__ __forceinline__ float rho(int k, int xs, int ys) const {
         return rho0[k * rho_plane + (long long)wrap(ys) * rho_row + xs];
     }
-    __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
+    static constexpr bool SPLIT = SplitStore<T>::value;
+    // stored value r^k_i of node (xs, ys): the deviation itself, or the split-form residual
+    __device__ __forceinline__ float res(int k, int i, int xs, int ys) const {
         return Codec<T>::dec(dev0[(k * 8 + i - 1) * dev_plane + (long long)wrap(ys) * dev_row + xs]);
+    }
+    // split-form shift h_i of node (xs, ys) (0 without the split form)
+    __device__ __forceinline__ float shift(int i, int xs, int ys) const {
+        if (!SPLIT) return 0.0f;
+        return split_shift(q, i, rho(0, xs, ys), rho(1, xs, ys), rho(2, xs, ys), rho(3, xs, ys), rho(4, xs, ys));
+    }
+    __device__ __forceinline__ float own_shift_sum(int xs, int ys) const {
+        return SPLIT ? 4.0f * rho(2, xs, ys) * (q.dph1 + q.dph2) : 0.0f;
+    }
+    // stored deviation d^k_i of node (xs, ys), decoded from the split form for 16-bit storage
+    __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
+        const float r = res(k, i, xs, ys);
+        if (!SPLIT) return r;
+        const float sh = shift(i, xs, ys);
+        return k == 0 ? __fadd_rn(r, sh) : __fsub_rn(r, sh);
     }
 };
 
 // Stored values from the shared-memory row ring (rows y-1, y, y+1 of a strip
-// starting at column x0).  A slot holds [2][BOXW] floats (padded to RHO_BYTES)
+// starting at column x0).  A slot holds [NS][BOXW] floats (padded to RHO_BYTES)
 // then [16][BOXW] T.
 template <typename T, int BOXW, int G, int RHO_BYTES>
 struct SmemLoader {
     const unsigned char *r0, *r1, *r2;
     int y, x0;
+    SplitC q;
     __device__ __forceinline__ const unsigned char *row(int ys) const {
         const int dy = ys - y;
         return dy < 0 ? r0 : (dy == 0 ? r1 : r2);
@@ -63,9 +83,23 @@ struct SmemLoader {
     __device__ __forceinline__ float rho(int k, int xs, int ys) const {
         return reinterpret_cast<const float *>(row(ys))[k * BOXW + (xs - x0 + G)];
     }
-    __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
+    static constexpr bool SPLIT = SplitStore<T>::value;
+    __device__ __forceinline__ float res(int k, int i, int xs, int ys) const {
         const T *p = reinterpret_cast<const T *>(row(ys) + RHO_BYTES);
         return Codec<T>::dec(p[(k * 8 + i - 1) * BOXW + (xs - x0 + G)]);
+    }
+    __device__ __forceinline__ float shift(int i, int xs, int ys) const {
+        if (!SPLIT) return 0.0f;
+        return split_shift(q, i, rho(0, xs, ys), rho(1, xs, ys), rho(2, xs, ys), rho(3, xs, ys), rho(4, xs, ys));
+    }
+    __device__ __forceinline__ float own_shift_sum(int xs, int ys) const {
+        return SPLIT ? 4.0f * rho(2, xs, ys) * (q.dph1 + q.dph2) : 0.0f;
+    }
+    __device__ __forceinline__ float dev(int k, int i, int xs, int ys) const {
+        const float r = res(k, i, xs, ys);
+        if (!SPLIT) return r;
+        const float sh = shift(i, xs, ys);
+        return k == 0 ? __fadd_rn(r, sh) : __fsub_rn(r, sh);
     }
     // same, for direction indices known only at run time
     __device__ __forceinline__ float rho_rt(int k, int xs, int ys) const { return rho(k, xs, ys); }
@@ -132,7 +166,8 @@ struct FusedCfg {
     static constexpr int GMEM = 8;                           // ghost columns kept in memory
     static constexpr int G = 16 / (int)sizeof(T);            // halo columns loaded each side
     static constexpr int BOXW = W + 2 * G;                   // TMA box width (elements)
-    static constexpr int RHO_BYTES = ((2 * BOXW * 4 + 127) / 128) * 128;
+    static constexpr int NS = ScalarPlanes<T>::value;          // FP32 node planes per row
+    static constexpr int RHO_BYTES = ((NS * BOXW * 4 + 127) / 128) * 128;
     static constexpr int DEV_BYTES = 16 * BOXW * (int)sizeof(T);
     static constexpr int SLOT_BYTES = ((RHO_BYTES + DEV_BYTES + 127) / 128) * 128;
     static constexpr int RING = W + 2;                       // ring width (columns x0-1 .. x0+W)
@@ -148,7 +183,7 @@ struct FusedCfg {
     static constexpr int DESC_BYTES = ((int)sizeof(SimDesc) + 127) / 128 * 128;
     static constexpr int RING_BYTES = ((RING_FLOATS * 4 + 15) / 16) * 16;
     static constexpr int SMEM = DESC_BYTES + NSLOT * SLOT_BYTES + RING_BYTES + NSLOT * 8 + 16;
-    static constexpr uint32_t TX_BYTES = (uint32_t)(2 * BOXW * 4 + DEV_BYTES);
+    static constexpr uint32_t TX_BYTES = (uint32_t)(NS * BOXW * 4 + DEV_BYTES);
     static_assert(BOXW <= 256, "TMA box dimension limit");
     static_assert((BOXW * sizeof(T)) % 16 == 0 && (BOXW * 4) % 16 == 0, "TMA inner box bytes");
     static_assert(G <= GMEM && G >= 3, "halo must cover the stencil and fit the memory ghost");
@@ -220,6 +255,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
         __syncthreads();
 
         const Phys p = d.ph;   // per-simulation constants, in registers from here on
+        const SplitC qs = split_consts(p);
         const long long t = d.t0 + step_offset;
         if (t >= d.t_end) continue;   // this simulation has stopped
         const int bsrc = (int)(t & 1), bdst = bsrc ^ 1;
@@ -252,7 +288,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
             const int xb = x0 + (Cfg::GMEM - G);   // element index of column x0 - G in the padded row
             mbar_arrive_expect_tx(&bars[s], Cfg::TX_BYTES);
             const int brow = bsrc * ny + yr;   // row index over both buffers
-            tma_load_2d(dst, &gd->tmap_rho, &bars[s], xb, brow * 2);
+            tma_load_2d(dst, &gd->tmap_rho, &bars[s], xb, brow * Cfg::NS);
             tma_load_2d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], xb, brow * 16);
         };
         int next_issue = row_first;   // meaningful on thread 0 only
@@ -276,6 +312,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
             L.r2 = row_ptr(y + 1);
             L.y = y;
             L.x0 = x0;
+            L.q = qs;
             return L;
         };
 
@@ -368,8 +405,9 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
                 s2i4(ring(ring_qy), gx_, dQy);
             }
             float dr[9], db[9];
-            collide_node<CV>(p, P, ring_psi[r0 + c], Fx, Fy, dQx, dQy, dr, db);
-            NodeStore<T>(d, p, bdst, x, y).store(P.rr, P.rb, dr, db);
+            float sm, sgx, sgy;
+            collide_node<CV, SplitStore<T>::value>(p, P, ring_psi[r0 + c], Fx, Fy, dQx, dQy, dr, db, sm, sgx, sgy);
+            NodeStore<T>(d, p, bdst, x, y).put(P.rr, P.rb, dr, db, sm, sgx, sgy);
         };
 
         // prologue: ring rows ya and ya - 1
@@ -498,8 +536,9 @@ __global__ void k_tp_collide(const SimDesc *__restrict__ dp, int step_offset, co
             s2i4([&](int dx, int dy) { return aux_at(p, aux + 4 * n, x + dx, y + dy, false); }, gx_, dQy);
         }
         float dr[9], db[9];
-        collide_node<CV>(p, P, aux[k], Fx, Fy, dQx, dQy, dr, db);
-        NodeStore<T>(d, p, bsrc ^ 1, x, y).store(P.rr, P.rb, dr, db);
+        float sm, sgx, sgy;
+        collide_node<CV, SplitStore<T>::value>(p, P, aux[k], Fx, Fy, dQx, dQy, dr, db, sm, sgx, sgy);
+        NodeStore<T>(d, p, bsrc ^ 1, x, y).put(P.rr, P.rb, dr, db, sm, sgx, sgy);
     }
 }
 

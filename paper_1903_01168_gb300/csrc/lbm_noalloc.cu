@@ -99,8 +99,9 @@ __global__ void k_na_collide(const __grid_constant__ SimDesc d, int step_offset,
             s2i4([&](int dx, int dy) { return aux_at(p, aux + 4 * n, x + dx, y + dy, false); }, gx_, dQy);
         }
         float dr[9], db[9];
-        collide_node<CV>(p, P, aux[k], Fx, Fy, dQx, dQy, dr, db);
-        NodeStore<T>(d, p, bsrc ^ 1, x, y).store(P.rr, P.rb, dr, db);
+        float sm, sgx, sgy;
+        collide_node<CV, SplitStore<T>::value>(p, P, aux[k], Fx, Fy, dQx, dQy, dr, db, sm, sgx, sgy);
+        NodeStore<T>(d, p, bsrc ^ 1, x, y).put(P.rr, P.rb, dr, db, sm, sgx, sgy);
     }
 }
 

@@ -5,10 +5,13 @@ type, number of steps) with an arrival time.  The server:
 
   * keeps every admitted simulation resident in device memory until it is done;
   * admits waiting requests in arrival order while the sum of the resident state
-    bytes stays within an HBM budget (first come, first served: a request that
-    does not fit blocks the ones behind it);
+    bytes stays within an HBM budget and the active lattice nodes stay within
+    `max_active_nodes`, about what it takes to keep every SM busy in one launch
+    (first come, first served: a request that does not fit blocks the ones
+    behind it).  Running more at once would only share the GPU among them and
+    delay every result;
   * advances all resident simulations together, one batched fused-kernel launch
-    per time step and storage type, in graph-captured chunks of steps; each
+    per time step and storage type, replaying a graph of `graph_steps` steps; each
     simulation carries its own stop step, so one that finishes inside a chunk
     simply stops there while the others go on;
   * between chunks retires the finished simulations (their diagnostics are read
@@ -30,7 +33,7 @@ import numpy as np
 from . import lbm as L
 from .workloads import SimSpec
 
-STORAGE_BYTES = {0: 144, 1: 80, 2: 80}
+STORAGE_BYTES = {0: 144, 1: 104, 2: 104}
 
 
 @dataclass
@@ -64,14 +67,19 @@ def state_bytes(spec: SimSpec) -> int:
 class Admission:
     """First-come-first-served admission under a byte budget (host logic only)."""
 
-    def __init__(self, budget_bytes: int):
+    def __init__(self, budget_bytes: int, max_active_nodes: int | None = None):
         self.budget = int(budget_bytes)
         self.resident = 0
+        self.max_nodes = None if max_active_nodes is None else int(max_active_nodes)
+        self.active_nodes = 0
 
-    def fits(self, nbytes: int) -> bool:
-        return self.resident + nbytes <= self.budget
+    def fits(self, nbytes: int, nodes: int = 0) -> bool:
+        if self.resident + nbytes > self.budget:
+            return False
+        # the node cap never holds back a request when nothing is active
+        return self.max_nodes is None or self.active_nodes == 0 or self.active_nodes + nodes <= self.max_nodes
 
-    def take(self, waiting: deque, now: float, size_of) -> list:
+    def take(self, waiting: deque, now: float, size_of, nodes_of=lambda r: 0) -> list:
         """Pop and return the requests that have arrived by `now` and fit, in
         arrival order, stopping at the first one that does not fit."""
         out = []
@@ -79,15 +87,18 @@ class Admission:
             nb = size_of(waiting[0])
             if nb > self.budget:
                 raise ValueError(f"request {waiting[0].rid} needs {nb} bytes, more than the whole budget")
-            if not self.fits(nb):
+            nn = nodes_of(waiting[0])
+            if not self.fits(nb, nn):
                 break
             self.resident += nb
+            self.active_nodes += nn
             out.append(waiting.popleft())
         return out
 
-    def release(self, nbytes: int):
+    def release(self, nbytes: int, nodes: int = 0):
         self.resident -= int(nbytes)
-        assert self.resident >= 0
+        self.active_nodes -= int(nodes)
+        assert self.resident >= 0 and self.active_nodes >= 0
 
 
 def params_of(spec: SimSpec) -> L.lbm_params:
@@ -130,20 +141,23 @@ class Server:
     """Continuous-batching server on the current CUDA device."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 500, max_chunk: int = 4000,
-                 use_graph: bool = False, clock=time.perf_counter, sleep=time.sleep):
-        self.admission = Admission(int(budget_bytes))
+                 graph_steps: int = 32, max_active_nodes: int | None = None,
+                 clock=time.perf_counter, sleep=time.sleep):
+        self.admission = Admission(int(budget_bytes), max_active_nodes)
         self.chunk = int(chunk)            # shortest chunk (bounds the wait of a new arrival)
         self.max_chunk = int(max_chunk)
-        self.use_graph = use_graph         # membership changes often: direct launches by default
+        self.graph_steps = int(graph_steps)   # steps per graph replay (0: direct launches only)
         self.clock = clock
         self.sleep = sleep
 
-    def _chunk_len(self, active, waiting) -> int:
-        """Run to the next completion, but no longer than max_chunk, and only
-        `chunk` steps when requests are waiting to be admitted."""
+    def _chunk_len(self, active, waiting, now: float) -> int:
+        """Run to the next completion, but no longer than max_chunk; only `chunk`
+        steps while the next request has not arrived yet (it may fit when it
+        does).  A request that has arrived and still waits is held back by the
+        budget or the node cap, which only a completion relieves."""
         left = min(r.spec.steps - s.t for s, r, _, _ in active.values())
         n = max(1, min(left, self.max_chunk))
-        if waiting:
+        if waiting and waiting[0].arrival > now:
             n = min(n, self.chunk)
         return n
 
@@ -157,7 +171,8 @@ class Server:
         t0 = self.clock()
         while waiting or active:
             now = self.clock() - t0
-            for r in self.admission.take(waiting, now, lambda q: state_bytes(q.spec)):
+            for r in self.admission.take(waiting, now, lambda q: state_bytes(q.spec),
+                                         lambda q: q.spec.nx * q.spec.ny):
                 s = start_simulation(r.spec)
                 s.set_stop(r.spec.steps)
                 active[r.rid] = (s, r, now, state_bytes(r.spec))
@@ -170,7 +185,15 @@ class Server:
                     batch.close()
                 batch = L.Batch([active[k][0] for k in key])
                 members = key
-            batch.step(self._chunk_len(active, waiting), use_graph=self.use_graph)
+            n = self._chunk_len(active, waiting, self.clock() - t0)
+            g = self.graph_steps
+            if g > 0 and n >= g:
+                # one graph of g steps per batch, replayed; the remainder launched directly
+                for _ in range(n // g):
+                    batch.step(g, use_graph=True)
+                n %= g
+            if n:
+                batch.step(n, use_graph=False)
             active[key[0]][0].synchronize()     # the batch runs on its first member's stream
             done = self.clock() - t0
             retired = []
@@ -187,7 +210,7 @@ class Server:
                 for k in retired:
                     s, r, adm, nb = active.pop(k)
                     s.close()
-                    self.admission.release(nb)
+                    self.admission.release(nb, r.spec.nx * r.spec.ny)
         if batch is not None:
             batch.close()
         makespan = self.clock() - t0

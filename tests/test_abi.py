@@ -45,7 +45,7 @@ def test_host_only_calls():
     # pitch = nx + 2 * 8 ghost columns rounded to 16 bytes
     assert L.lbm_bytes_required(64, 32, p) == 2 * 2 * 32 * 80 * 4 + 2 * 16 * 32 * 80 * 4
     p.storage = L.LBM_F16DEV
-    assert L.lbm_bytes_required(64, 32, p) == 2 * 2 * 32 * 80 * 4 + 2 * 16 * 32 * 80 * 2
+    assert L.lbm_bytes_required(64, 32, p) == 2 * 5 * 32 * 80 * 4 + 2 * 16 * 32 * 80 * 2
     bad = L.lbm_default_params()
     bad.tau_r = 0.5
     assert L.lbm_bytes_required(64, 32, bad) == 0

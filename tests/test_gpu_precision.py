@@ -1,11 +1,13 @@
-"""Reduced-precision storage (FP16 / BF16 deviations from the rest state of each
-colour, FP32 arithmetic, FP32 colour densities) against the FP64 oracle.
+"""Reduced-precision storage (FP16 / BF16 deviations in the split form: the
+recolouring shift and flux rebuilt from FP32 node scalars, only the colour-blind
+remainder rounded to 16 bits; FP32 arithmetic and colour densities) against the
+FP64 oracle.
 
-Bars follow from the storage precision: deviations are rounded to 2^-11 (FP16)
-or 2^-8 (BF16) of their size each step, so fields after 100 steps carry errors of
-that relative order; per-colour mass lives in the FP32 densities and stays
-conserved to FP32 round-off.  Integral diagnostics are compared with the
-oracle's: the slug (light-phase) velocity and the Laplace jump."""
+Field bars follow from the storage precision: the stored remainders are rounded
+to 2^-11 (FP16) or 2^-8 (BF16) of their size each step.  Per-colour mass lives in
+the FP32 densities and stays conserved to FP32 round-off.  The integral
+diagnostics, slug (light-phase) velocity and Laplace jump, are held to 1 % of the
+oracle's for both storage types."""
 import numpy as np
 import pytest
 
@@ -23,7 +25,7 @@ def _native():
     L.load(build_if_missing=True)
 
 
-@pytest.mark.parametrize("storage,tol_rho,tol_u", [(F16, 2e-3, 1e-2), (BF16, 2e-2, 1e-1)])
+@pytest.mark.parametrize("storage,tol_rho,tol_u", [(F16, 1e-3, 5e-3), (BF16, 5e-3, 5e-2)])
 def test_parity_100_steps_within_storage_precision(storage, tol_rho, tol_u):
     nx, ny = 200, 37
     kw = dict(gamma=10.0, tau_r=0.6, tau_b=1.1, sigma=0.01, beta=0.7, collision=L.LBM_MRT,
@@ -55,7 +57,7 @@ def test_colour_mass_conserved_with_16bit_deviations(storage):
         assert abs(d1[k] - d0[k]) <= 1e-6 * d0[k]
 
 
-@pytest.mark.parametrize("storage,tol", [(F16, 0.01), (BF16, 0.03)])
+@pytest.mark.parametrize("storage,tol", [(F16, 0.01), (BF16, 0.01)])
 def test_slug_velocity_vs_oracle(storage, tol):
     """Gravity-driven periodic slug (walls, gamma = 10, Re = 50, Bo = 0.7848), 4000
     steps: light-phase mean x-velocity against the oracle's."""
@@ -79,11 +81,12 @@ def test_slug_velocity_vs_oracle(storage, tol):
     assert rel <= tol
 
 
-@pytest.mark.parametrize("storage,tol", [(F16, 0.05), (BF16, 0.25)])
+@pytest.mark.parametrize("storage,tol", [(F16, 0.01), (BF16, 0.01)])
 def test_laplace_jump_vs_oracle(storage, tol):
     """64^2 static bubble, 2000 steps.  The jump is 3.3e-4 of a pressure of 0.48,
-    i.e. the density varies by ~7e-4 across the interface: deviation rounding in
-    the interface band moves it by a few percent (FP16) or more (BF16)."""
+    i.e. the density varies by ~7e-4 across the interface.  Rounding the full
+    per-colour deviations (O(rho_r rho_b / rho) at the interface) to 16 bits moved
+    it by 2.5 % (FP16) to 14 % (BF16); the split form keeps both within 1 %."""
     o = O.Oracle(O.OracleParams(nx=64, ny=64, gamma=1.0, sigma=0.005, beta=0.7))
     o.init_fields(*W.bubble_fields(64, 64, 32, 32, 16, 1.0))
     o.step(2000)

@@ -26,10 +26,13 @@ def _trace():
     ]
 
 
-def test_each_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("max_active_nodes", [4_000_000, 20_000])
+def test_each_result_is_the_same_alone_and_in_the_mix(max_active_nodes):
+    """Every request's diagnostics equal those of the same simulation run alone,
+    whether all requests share the GPU or the node cap admits them a few at a time."""
     L.load(build_if_missing=True)
     trace = _trace()
-    results, stats = S.Server(budget_bytes=2e9, chunk=64).run(trace)
+    results, stats = S.Server(budget_bytes=2e9, chunk=64, max_active_nodes=max_active_nodes).run(trace)
     assert stats["requests"] == len(trace)
     for r, (_, spec) in zip(results, trace):
         with S.start_simulation(spec) as s:

@@ -28,6 +28,23 @@ def test_admits_in_arrival_order_within_budget():
     assert [r.rid for r in got] == [3] and a.resident == 71
 
 
+def test_active_node_cap_holds_back_later_requests():
+    a = Admission(1000, max_active_nodes=100)
+    q = deque([_req(0, 0.0, 1), _req(1, 0.0, 1), _req(2, 0.0, 1)])
+    nodes = {0: 60, 1: 50, 2: 30}
+    got = a.take(q, now=0.0, size_of=lambda r: r.nbytes, nodes_of=lambda r: nodes[r.rid])
+    assert [r.rid for r in got] == [0]              # 60 + 50 > 100, and FCFS keeps 2 behind 1
+    a.release(1, 60)
+    got = a.take(q, now=0.0, size_of=lambda r: r.nbytes, nodes_of=lambda r: nodes[r.rid])
+    assert [r.rid for r in got] == [1, 2] and a.active_nodes == 80
+
+
+def test_node_cap_never_blocks_an_idle_server():
+    a = Admission(1000, max_active_nodes=10)
+    got = a.take(deque([_req(0, 0.0, 1)]), now=0.0, size_of=lambda r: r.nbytes, nodes_of=lambda r: 500)
+    assert [r.rid for r in got] == [0]
+
+
 def test_request_larger_than_budget_is_an_error():
     a = Admission(10)
     with pytest.raises(ValueError):
