@@ -141,7 +141,7 @@ class Server:
     """Continuous-batching server on the current CUDA device."""
 
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 500, max_chunk: int = 4000,
-                 graph_steps: int = 32, max_active_nodes: int | None = None,
+                 graph_steps: int = 32, max_active_nodes: int | None = 8_000_000,
                  clock=time.perf_counter, sleep=time.sleep):
         self.admission = Admission(int(budget_bytes), max_active_nodes)
         self.chunk = int(chunk)            # shortest chunk (bounds the wait of a new arrival)

@@ -135,7 +135,7 @@ class SimSpec:
     gy: float = 0.0
     bc_x: int = 0          # 0 periodic, 1 wall, 2 inlet/outlet
     bc_y: int = 0
-    geometry: str = "bubble"   # "bubble" | "slug" | "inout"
+    geometry: str = "bubble"   # "bubble" | "slug" | "inout" | "rayleigh_taylor"
     bubble: tuple = ()         # (cx, cy, R)
     slug: tuple = ()           # (n_bubbles, length, height)
     steps: int = 0
@@ -244,6 +244,39 @@ def serving_trace(seed: int = DEFAULT_SEED, n_requests: int = 32, rate_hz: float
                                storage=storage, u_in_r=1.25e-2, u_in_b=7.5e-2,
                                p_out=0.48, inlet_period_r=400, inlet_period_b=200)))
     return out
+
+
+def rayleigh_taylor(L: int = 140, amp: float = 0.15, storage: int = 0) -> SimSpec:
+    """Rayleigh-Taylor instability as in the paper's two-phase cases: an L x 2L box
+    (about 40 000 nodes), heavy fluid (red, gamma = 1.8) above light fluid,
+    viscosity ratio 1, no surface tension, gravity 1e-4 l.u. downwards.  The
+    viscosity follows from Re = sqrt((H/2)^3 g) / nu = 420 with H = 2L.  The
+    interface is y = H/2 - amp L sin(2 pi x / L).  The printed amplitude of that
+    formula (1, in units of L) would reach both walls; 0.15 L is the cited setup's
+    value.  No-slip walls at the bottom and top.  The lattice has walls in y only,
+    so x is periodic.  Time unit t_g = sqrt(H / g)."""
+    H = 2 * L
+    g = 1e-4
+    nu = math.sqrt((H / 2.0) ** 3 * g) / 420.0
+    tau = tau_of_nu(nu)
+    t_g = math.sqrt(H / g)
+    return SimSpec(nx=L, ny=H, gamma=1.8, tau_r=tau, tau_b=tau, sigma=0.0, beta=0.7, gx=0.0, gy=-g,
+                   bc_x=0, bc_y=1, geometry="rayleigh_taylor", steps=int(round(5 * t_g)), storage=storage,
+                   extra={"amp": amp, "t_g": t_g, "nu": nu})
+
+
+def rayleigh_taylor_fields(nx: int, ny: int, gamma: float, amp: float):
+    """Sharp interface y = ny/2 - amp nx sin(2 pi (x + 1/2) / nx) (node centres at
+    x + 1/2, so the field is mirror-symmetric about x = nx/4 for even nx): heavy
+    (red, rho = gamma) above, light (blue, rho = 1) below, at rest."""
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny)[:, None] + 0.5
+    yi = ny / 2.0 - amp * nx * np.sin(2.0 * np.pi * x / nx)[None, :]
+    heavy = y >= yi
+    rr = np.where(heavy, gamma, 0.0)
+    rb = np.where(heavy, 0.0, 1.0)
+    z = np.zeros((ny, nx))
+    return rr, rb, z, z.copy()
 
 
 def poiseuille_profile(ny: int, g: float, nu: float) -> np.ndarray:
