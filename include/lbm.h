@@ -114,6 +114,17 @@ typedef struct {
                             re-reading.  Never changes results, only speed (the
                             Python autotuner picks it per lattice size class). */
     int plan;            /* lbm_plan_kind of this lattice's own launches (0 = AUTO) */
+    int wall_slip;       /* walls (bc_y = WALL): 0 no slip (halfway bounce-back), 1 free
+                            slip: diagonal populations travel on along the wall,
+                            mirrored (Sec. 2.5 "Boundary conditions").  Free slip and a
+                            contact angle (below) run on the two-pass kernels: kernel
+                            FUSED is then LBM_EINVAL, AUTO takes TWOPASS, and such a
+                            lattice cannot join a batch */
+    double contact_angle;/* static contact angle on the walls, radians in (0, pi), measured
+                            through the blue phase; 0 = no adjustment.  On the fluid rows
+                            next to a wall the colour gradient is turned to the closer of
+                            the two normals at this angle from the wall normal (Sec.
+                            "Adjustment of the color gradient for static contact angles") */
 } lbm_params;
 
 /* FP64 diagnostics of the state at the current time t (sums over all nodes). */

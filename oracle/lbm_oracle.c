@@ -52,6 +52,10 @@
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+/* mirror images of each direction in a horizontal wall (c_y -> -c_y) and in a
+ * vertical one (c_x -> -c_x): where a free-slip wall sends a population */
+static const int MIRY[9] = {0, 1, 4, 3, 2, 8, 7, 6, 5};
+static const int MIRX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
 
 static int c2(int i) { return CX[i] * CX[i] + CY[i] * CY[i]; }
 
@@ -561,6 +565,35 @@ static void gradient_node(const orc_sim *s, int x, int y, double *Fx, double *Fy
     }
 }
 
+/* Static contact angle (Sec. "Adjustment of the color gradient for static
+ * contact angles"): at a fluid node next to a wall (class C_fs) the direction
+ * n* = F / |F| is replaced by whichever of the two unit normals n1, n2 that make
+ * the angle theta with the wall normal n^s (pointing into the fluid) is closer to
+ * it, n^s itself on a tie; |F| is kept.  Applied to walls in y (a node next to
+ * both walls of a one-row channel takes the bottom one). */
+static void contact_angle_adjust(const orc_params *p, int x, int y, double *Fx, double *Fy) {
+    (void)x;
+    if (p->contact_angle <= 0.0 || p->bc_y != ORC_WALL) return;
+    double nsx = 0.0, nsy;
+    if (y == 0) nsy = 1.0;
+    else if (y == p->ny - 1) nsy = -1.0;
+    else return;
+    double F = sqrt(*Fx * *Fx + *Fy * *Fy);
+    if (F == 0.0) return;
+    double ct = cos(p->contact_angle), st = sin(p->contact_angle);
+    double n1x = nsx * ct - nsy * st, n1y = nsy * ct + nsx * st;
+    double n2x = nsx * ct + nsy * st, n2y = nsy * ct - nsx * st;
+    double ux = *Fx / F, uy = *Fy / F;
+    double d1 = sqrt((ux - n1x) * (ux - n1x) + (uy - n1y) * (uy - n1y));
+    double d2 = sqrt((ux - n2x) * (ux - n2x) + (uy - n2y) * (uy - n2y));
+    double nx_, ny_;
+    if (d1 < d2) { nx_ = n1x; ny_ = n1y; }
+    else if (d1 > d2) { nx_ = n2x; ny_ = n2y; }
+    else { nx_ = nsx; ny_ = nsy; }
+    *Fx = F * nx_;
+    *Fy = F * ny_;
+}
+
 void orc_gradient_fields(orc_sim *s, double *Fx, double *Fy, double *dQ) {
     moments_pass(s);
     int nx = s->p.nx, ny = s->p.ny;
@@ -570,6 +603,7 @@ void orc_gradient_fields(orc_sim *s, double *Fx, double *Fy, double *dQ) {
             size_t c = (size_t)y * nx + x;
             double fx, fy, d[2][2];
             gradient_node(s, x, y, &fx, &fy, d);
+            contact_angle_adjust(&s->p, x, y, &fx, &fy);
             if (Fx) Fx[c] = fx;
             if (Fy) Fy[c] = fy;
             if (dQ) {
@@ -594,6 +628,7 @@ static void step_once(orc_sim *s) {
             size_t c = (size_t)y * nx + x;
             double Fx, Fy, dQ[2][2];
             gradient_node(s, x, y, &Fx, &Fy, dQ);
+            contact_angle_adjust(p, x, y, &Fx, &Fy);
             double Nk[18], Nstar[18], Nsum[9], Nr[9], Nb[9];
             gather_node(s, s->N, x, y, Nk);
             orc_collide_node(p, Nk, Fx, Fy, dQ[0][0], dQ[0][1], dQ[1][0], dQ[1][1], Nstar);
@@ -614,9 +649,16 @@ static void step_once(orc_sim *s) {
                     int xw, yw;
                     double v;
                     int out_y = (Y < 0 || Y >= ny), out_x = (X < 0 || X >= nx);
+                    int wall_y = out_y && p->bc_y == ORC_WALL, wall_x = out_x && p->bc_x == ORC_WALL;
                     if (in_domain(p, X, Y, &xw, &yw))
                         v = s->Npost[pidx(s, k, i, xw, yw)];
-                    else if ((out_y && p->bc_y == ORC_WALL) || (out_x && p->bc_x == ORC_WALL))
+                    else if (p->wall_slip && wall_y && in_domain(p, X, y, &xw, &yw))
+                        /* free slip: the population left (X, y) towards the wall and
+                         * comes back mirrored, travelling on along the wall */
+                        v = s->Npost[pidx(s, k, MIRY[i], xw, yw)];
+                    else if (p->wall_slip && wall_x && in_domain(p, x, Y, &xw, &yw))
+                        v = s->Npost[pidx(s, k, MIRX[i], xw, yw)];
+                    else if (wall_y || wall_x)
                         v = s->Npost[pidx(s, k, OPP[i], x, y)]; /* halfway bounce-back */
                     else
                         v = 0.0; /* unknown, set by Zou-He below */

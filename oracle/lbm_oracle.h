@@ -50,6 +50,10 @@ typedef struct {
     int inlet_mode;     /* ORC_INLET_ALTERNATE (in time) / ORC_INLET_LAYERED (in y) */
     int inlet_period_r, inlet_period_b; /* steps of red then blue injection */
     int inlet_layer;    /* rows y < inlet_layer inject red when layered */
+    int wall_slip;      /* walls: 0 no slip (halfway bounce-back), 1 free slip (Sec. 2.5) */
+    double contact_angle; /* radians, 0 < theta < pi; 0 = no colour-gradient adjustment
+                             (Sec. "Adjustment of the color gradient for static contact
+                             angles"); theta is measured through the blue phase */
 } orc_params;
 
 typedef struct orc_sim orc_sim;

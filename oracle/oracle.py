@@ -42,6 +42,7 @@ class _Params(ctypes.Structure):
         ("u_in_r", ctypes.c_double), ("u_in_b", ctypes.c_double), ("p_out", ctypes.c_double),
         ("inlet_mode", ctypes.c_int), ("inlet_period_r", ctypes.c_int),
         ("inlet_period_b", ctypes.c_int), ("inlet_layer", ctypes.c_int),
+        ("wall_slip", ctypes.c_int), ("contact_angle", ctypes.c_double),
     ]
 
 
@@ -74,6 +75,8 @@ class OracleParams:
     inlet_period_r: int = 0
     inlet_period_b: int = 0
     inlet_layer: int = 0
+    wall_slip: int = 0
+    contact_angle: float = 0.0
 
     def to_c(self) -> _Params:
         return _Params(**{f.name: getattr(self, f.name) for f in fields(self)})

@@ -160,6 +160,15 @@ lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
     if (p->kernel < 0 || p->kernel > 2) { set_err(err, "unknown kernel"); return LBM_EINVAL; }
     if (p->plan_rows < 0 || p->plan_rows > (1 << 20)) { set_err(err, "plan_rows out of range"); return LBM_EINVAL; }
     if (p->plan < LBM_PLAN_AUTO || p->plan > LBM_PLAN_SPLIT) { set_err(err, "unknown plan kind"); return LBM_EINVAL; }
+    if (p->wall_slip != 0 && p->wall_slip != 1) { set_err(err, "wall_slip must be 0 or 1"); return LBM_EINVAL; }
+    if (p->kernel == LBM_KERNEL_FUSED && (p->wall_slip != 0 || p->contact_angle > 0.0)) {
+        set_err(err, "wetting walls run on the two-pass kernel (kernel AUTO or TWOPASS)");
+        return LBM_EINVAL;
+    }
+    if (!(p->contact_angle >= 0.0 && p->contact_angle < 3.14159265358979)) {
+        set_err(err, "contact_angle must be 0 (off) or in (0, pi) radians");
+        return LBM_EINVAL;
+    }
     if (p->bc_x == LBM_BC_INOUT && !(p->p_out > 0.0)) {
         set_err(err, "inlet/outlet needs p_out > 0");
         return LBM_EINVAL;
@@ -253,6 +262,10 @@ void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     f.u_in_r = (float)p->u_in_r;
     f.u_in_b = (float)p->u_in_b;
     f.p_out = (float)p->p_out;
+    h.wet.slip = p->wall_slip;
+    h.wet.on = p->contact_angle > 0.0 ? 1 : 0;
+    h.wet.cos_t = (float)cos(p->contact_angle);
+    h.wet.sin_t = (float)sin(p->contact_angle);
 }
 
 lbm_status encode_tmap(lbm_sim *s) {
@@ -603,7 +616,10 @@ void launch_diag(lbm_sim *s, int pass, double cx, double cy, double rin, double 
     }
 }
 
-bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS; }
+// Wetting walls (free slip, contact angle) run on the two-pass kernels: the
+// fused kernel is compiled for no-slip walls only.
+bool wetting(const lbm_params *p) { return p->wall_slip != 0 || p->contact_angle > 0.0; }
+bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS && !wetting(&s->p); }
 
 lbm_status sync_t0(lbm_sim *s) {
     if (s->dev_t0 != s->t) {
@@ -739,7 +755,8 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         }
     }
     const size_t nn = (size_t)nx * ny;
-    if (p->kernel == LBM_KERNEL_TWOPASS && cudaMalloc(&s->d_aux, AUX_FIELDS * nn * sizeof(float)) != cudaSuccess) {
+    if ((p->kernel == LBM_KERNEL_TWOPASS || wetting(p)) &&
+        cudaMalloc(&s->d_aux, AUX_FIELDS * nn * sizeof(float)) != cudaSuccess) {
         set_err(s->err, "cudaMalloc of scratch field failed");
         return fail(LBM_ENOMEM);
     }
@@ -1107,6 +1124,10 @@ lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts
     for (int i = 0; i < n; i++) {
         if (!sims[i] || sims[i]->dev != sims[0]->dev) {
             set_err(g_create_err, "batch members must exist and share a device");
+            return LBM_EINVAL;
+        }
+        if (wetting(&sims[i]->p)) {
+            set_err(g_create_err, "member %d has wetting walls (two-pass kernel only); batches run the fused kernel", i);
             return LBM_EINVAL;
         }
         strip_rows += (long long)((sims[i]->nx + FUSED_W - 1) / FUSED_W) * sims[i]->ny;

@@ -73,6 +73,40 @@ struct Phys {
     float u_in_r, u_in_b, p_out;
 };
 
+// Wetting-wall parameters (free slip, static contact angle).  Kept out of Phys:
+// the fused kernel, which holds Phys in registers, never runs such lattices.
+struct Wetting {
+    int slip;                  // walls: 0 no slip, 1 free slip
+    int on;                    // 1: contact-angle adjustment of F next to the walls
+    float cos_t, sin_t;        // of the contact angle (measured through the blue phase)
+};
+
+// Static contact angle (Sec. "Adjustment of the color gradient for static
+// contact angles"): on the fluid rows next to a wall the direction of F is
+// replaced by whichever of the two unit normals at angle theta from the wall
+// normal n^s (into the fluid) is closer to it (n^s itself on a tie), |F| kept.
+__device__ __forceinline__ void contact_angle_adjust(const Wetting &wt, const Phys &p, int y, float &Fx, float &Fy) {
+    if (!wt.on || p.bc_y != BC_WALL || (y != 0 && y != p.ny - 1)) return;
+    const float nsy = y == 0 ? 1.0f : -1.0f;   // n^s = (0, nsy)
+    const float F2 = Fx * Fx + Fy * Fy;
+    if (F2 == 0.0f) return;
+    const float F = sqrtf(F2), ux = Fx / F, uy = Fy / F;
+    // n1 = (-nsy sin, nsy cos), n2 = (nsy sin, nsy cos); compared by squared distance
+    const float n1x = -nsy * wt.sin_t, n2x = nsy * wt.sin_t, ny_ = nsy * wt.cos_t;
+    const float d1 = (ux - n1x) * (ux - n1x) + (uy - ny_) * (uy - ny_);
+    const float d2 = (ux - n2x) * (ux - n2x) + (uy - ny_) * (uy - ny_);
+    if (d1 < d2) {
+        Fx = F * n1x;
+        Fy = F * ny_;
+    } else if (d1 > d2) {
+        Fx = F * n2x;
+        Fy = F * ny_;
+    } else {
+        Fx = 0.0f;
+        Fy = F * nsy;
+    }
+}
+
 struct alignas(128) SimDesc {
     CUtensorMap tmap_rho;      // 2D {pitch_r, 2 * ny * 2} box {W + 2 halo, 2}: one row's 2 planes
     CUtensorMap tmap_dev;      // 2D {pitch_d, 2 * ny * 16} box {W + 2 halo, 16}: one row's 16 planes
@@ -85,6 +119,7 @@ struct alignas(128) SimDesc {
     int pitch_r, pitch_d, ghost;
     int storage, variant;      // variant: bit 0 MRT, bit 1 Hermite equilibrium
     Phys ph;
+    Wetting wet;
 };
 
 // Collision variants (compile-time): bit 0 = MRT (else BGK), bit 1 = Hermite
@@ -281,6 +316,34 @@ struct Pulled {
     float e[9];
 };
 
+// Where direction i of node (x, y) pulls from: the node x - c_i, or across a
+// wall (Sec. 2.5) the node itself in direction OPP(i) (no slip, halfway
+// bounce-back), or with free slip the node x - (c_ix, 0) of the same row in the
+// mirrored direction (the population travels on along the wall).  Free slip
+// falls back to bounce-back where that node is outside an open lattice (the
+// Zou-He columns then overwrite the link).
+struct Link {
+    int xs, ys, ii;
+    bool self;   // the source is the node itself
+};
+
+__host__ __device__ constexpr int MIRY(int i) { return i == 2 ? 4 : i == 4 ? 2 : i == 5 ? 8 : i == 8 ? 5 : i == 6 ? 7 : i == 7 ? 6 : i; }
+
+// Link sets a pull is compiled for: no-slip walls only (the fused kernel, which
+// never runs lattices with wetting walls: their extra logic would cost the hot
+// loop registers on every row), or no-slip and free-slip walls (all others).
+constexpr int LINKS_NOSLIP = 1, LINKS_ALL = 2;
+
+template <int LINKS>
+__device__ __forceinline__ Link link_of(const Phys &p, int slip, int i, int x, int y, bool bottom, bool top) {
+    const bool wall = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+    if (!wall) return Link{x - CX(i), y - CY(i), i, false};
+    if (LINKS == LINKS_NOSLIP) return Link{x, y, OPP(i), true};
+    const int xs = x - CX(i);
+    if (slip && (p.bc_x == BC_PERIODIC || (xs >= 0 && xs < p.nx))) return Link{xs, y, MIRY(i), CX(i) == 0};
+    return Link{x, y, OPP(i), true};
+}
+
 // Pull the pre-collision populations of node (x, y) at time t (Eq. (eq:subop4)):
 // N^k_i(x) = phi^k_i rho_k(x - c_i) + d^k_i(x - c_i), with halfway bounce-back
 // across walls (the node's own opposite population) and two-phase Zou-He on
@@ -297,27 +360,32 @@ struct Pulled {
 //   sum_i h_i(source of i) - sum_i h_i(x),
 // where the node's own sum is 4 m (dphi_1 + dphi_2) (the flux parts cancel in
 // opposite pairs).
-template <class Loader>
+template <int LINKS, class Loader>
 __device__ __forceinline__ void pull_node_split(const Phys &p, const Loader &ld, int x, int y, bool have_rho,
                                                 float rr_new, float rb_new, Pulled &P) {
     const bool wall_y = p.bc_y == BC_WALL;
     const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
-    float s[2][9], rs[2][9], own_rho[2];
-    own_rho[0] = ld.rho(0, x, y);
-    own_rho[1] = ld.rho(1, x, y);
-    float hsum = 0.0f;
+    float own[2];
+    own[0] = ld.rho(0, x, y);
+    own[1] = ld.rho(1, x, y);
+    // one pass over the links, keeping per direction only
+    //   T_i = sum_k phi^k_i (s^k_i - rho_k(x)) + r^r_i + r^b_i
+    // (small terms) and the colour sums; then e_i = T_i - sum_k phi^k_i (rho'_k - rho_k(x))
+    float T[9], acc[2] = {0.0f, 0.0f}, hsum = 0.0f;
 #pragma unroll
     for (int i = 1; i < 9; i++) {
-        const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
-        const int xs = bounce ? x : x - CX(i), ys = bounce ? y : y - CY(i);
-        const int ii = bounce ? OPP(i) : i;
+        const Link lk = link_of<LINKS>(p, ld.slip, i, x, y, bottom, top);
+        const int xs = lk.xs, ys = lk.ys, ii = lk.ii;
+        float ti = 0.0f;
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-            s[k][i] = bounce ? own_rho[k] : ld.rho(k, xs, ys);
-            rs[k][i] = ld.res(k, ii, xs, ys);
+            const float ds = (lk.self ? own[k] : ld.rho(k, xs, ys)) - own[k];
+            const float r = ld.res(k, ii, xs, ys);
+            const float f = phi_k(p, k, C2(i)) * ds;
+            acc[k] += f + (r - ld.res(k, i, x, y));
+            ti += f + r;
         }
-        // evaluated for every node: skipping it where all densities are pure (where
-        // it is exactly zero) leaves the warps of a block unbalanced at the row barrier
+        T[i] = ti;
         hsum += ld.shift(ii, xs, ys);
     }
     float rnew[2];
@@ -326,34 +394,29 @@ __device__ __forceinline__ void pull_node_split(const Phys &p, const Loader &ld,
         rnew[1] = rb_new;
     } else {
         const float dh = hsum - ld.own_shift_sum(x, y);
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int i = 1; i < 9; i++)
-                acc += phi_k(p, k, C2(i)) * (s[k][i] - own_rho[k]) + (rs[k][i] - ld.res(k, i, x, y));
-            rnew[k] = own_rho[k] + (k == 0 ? acc + dh : acc - dh);
-        }
+        rnew[0] = own[0] + (acc[0] + dh);
+        rnew[1] = own[1] + (acc[1] - dh);
     }
     P.rr = rnew[0];
     P.rb = rnew[1];
+    const float dr = rnew[0] - own[0], db = rnew[1] - own[1];
     float e0 = 0.0f;
 #pragma unroll
     for (int i = 1; i < 9; i++) {
-        P.e[i] = p.phi_r[C2(i)] * (s[0][i] - rnew[0]) + rs[0][i] + p.phi_b[C2(i)] * (s[1][i] - rnew[1]) + rs[1][i];
+        P.e[i] = T[i] - (p.phi_r[C2(i)] * dr + p.phi_b[C2(i)] * db);
         e0 += P.e[i];
     }
     P.e[0] = -e0;
 }
 
-template <bool HERMITE, class Loader>
-__device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x, int y, long long t,
-                                          bool have_rho, float rr_new, float rb_new, Pulled &P) {
+template <bool HERMITE, int LINKS, class Loader>
+__device__ __forceinline__ void pull_node_rows(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                               bool have_rho, float rr_new, float rb_new, Pulled &P) {
     const bool wall_y = p.bc_y == BC_WALL;
     const bool open_col = p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1);
     const bool bottom = wall_y && y == 0, top = wall_y && y == p.ny - 1;
     if (Loader::SPLIT && !open_col) {
-        pull_node_split(p, ld, x, y, have_rho, rr_new, rb_new, P);
+        pull_node_split<LINKS>(p, ld, x, y, have_rho, rr_new, rb_new, P);
         return;
     }
     float s[2][9], dl[2][9], own_rho[2];
@@ -362,13 +425,20 @@ __device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x
         own_rho[k] = ld.rho(k, x, y);
 #pragma unroll
         for (int i = 1; i < 9; i++) {
-            const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
-            if (bounce) {
-                s[k][i] = own_rho[k];
-                dl[k][i] = ld.dev(k, OPP(i), x, y);
+            if (LINKS == LINKS_NOSLIP) {
+                // constant plane offsets in both branches (no run-time direction index)
+                const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+                if (bounce) {
+                    s[k][i] = own_rho[k];
+                    dl[k][i] = ld.dev(k, OPP(i), x, y);
+                } else {
+                    s[k][i] = ld.rho(k, x - CX(i), y - CY(i));
+                    dl[k][i] = ld.dev(k, i, x - CX(i), y - CY(i));
+                }
             } else {
-                s[k][i] = ld.rho(k, x - CX(i), y - CY(i));
-                dl[k][i] = ld.dev(k, i, x - CX(i), y - CY(i));
+                const Link lk = link_of<LINKS>(p, ld.slip, i, x, y, bottom, top);
+                s[k][i] = lk.self ? own_rho[k] : ld.rho(k, lk.xs, lk.ys);
+                dl[k][i] = ld.dev(k, lk.ii, lk.xs, lk.ys);
             }
         }
     }
@@ -424,15 +494,22 @@ __device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x
     for (int i = 0; i < 9; i++) P.e[i] = (nr[i] + nb[i]) - (rr * p.phi_r[C2(i)] + rb * p.phi_b[C2(i)]);
 }
 
+// Pull with every kind of wall link.
+template <bool HERMITE, class Loader>
+__device__ __forceinline__ void pull_node(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                          bool have_rho, float rr_new, float rb_new, Pulled &P) {
+    pull_node_rows<HERMITE, LINKS_ALL>(p, ld, x, y, t, have_rho, rr_new, rb_new, P);
+}
+
 // Moments of the pulled node (x, y) without forming its populations: the new
 // colour densities
 //   rho_k' = rho_k(x) + sum_{i>=1} [phi^k_i (s^k_i - rho_k(x)) + delta^k_i - d^k_i(x)]
 // (s, delta: density and deviation of the source of direction i) and, with
 // NEED_J, the momentum sum_i c_i N_i summed over opposite pairs.  Open columns
 // take the full pull.
-template <bool HERMITE, bool NEED_J, class Loader>
-__device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, int x, int y, long long t,
-                                             float &rr, float &rb, float &jx, float &jy) {
+template <bool HERMITE, bool NEED_J, int LINKS, class Loader>
+__device__ __forceinline__ void pull_moments_rows(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                                  float &rr, float &rb, float &jx, float &jy) {
     if (p.bc_x == BC_INOUT && (x == 0 || x == p.nx - 1)) {
         Pulled P;
         pull_node<HERMITE>(p, ld, x, y, t, false, 0.0f, 0.0f, P);
@@ -453,12 +530,11 @@ __device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, in
         own[1] = ld.rho(1, x, y);
 #pragma unroll
         for (int i = 1; i < 9; i++) {
-            const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
-            const int xs = bounce ? x : x - CX(i), ys = bounce ? y : y - CY(i);
-            const int ii = bounce ? OPP(i) : i;
+            const Link lk = link_of<LINKS>(p, ld.slip, i, x, y, bottom, top);
+            const int xs = lk.xs, ys = lk.ys, ii = lk.ii;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                const float sv = bounce ? own[k] : ld.rho(k, xs, ys);
+                const float sv = lk.self ? own[k] : ld.rho(k, xs, ys);
                 n[k][i] = phi_k(p, k, C2(i)) * (sv - own[k]) + ld.res(k, ii, xs, ys);
             }
             hsum += ld.shift(ii, xs, ys);
@@ -493,14 +569,20 @@ __device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, in
         float a = 0.0f;
 #pragma unroll
         for (int i = 1; i < 9; i++) {
-            const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
             float sv, dv;
-            if (bounce) {
-                sv = own;
-                dv = ld.dev(k, OPP(i), x, y);
+            if (LINKS == LINKS_NOSLIP) {
+                const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
+                if (bounce) {
+                    sv = own;
+                    dv = ld.dev(k, OPP(i), x, y);
+                } else {
+                    sv = ld.rho(k, x - CX(i), y - CY(i));
+                    dv = ld.dev(k, i, x - CX(i), y - CY(i));
+                }
             } else {
-                sv = ld.rho(k, x - CX(i), y - CY(i));
-                dv = ld.dev(k, i, x - CX(i), y - CY(i));
+                const Link lk = link_of<LINKS>(p, ld.slip, i, x, y, bottom, top);
+                sv = lk.self ? own : ld.rho(k, lk.xs, lk.ys);
+                dv = ld.dev(k, lk.ii, lk.xs, lk.ys);
             }
             n[k][i] = phi_k(p, k, C2(i)) * (sv - own) + dv;
             a += n[k][i] - ld.dev(k, i, x, y);
@@ -520,6 +602,12 @@ __device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, in
     }
 }
 
+template <bool HERMITE, bool NEED_J, class Loader>
+__device__ __forceinline__ void pull_moments(const Phys &p, const Loader &ld, int x, int y, long long t,
+                                             float &rr, float &rb, float &jx, float &jy) {
+    pull_moments_rows<HERMITE, NEED_J, LINKS_ALL>(p, ld, x, y, t, rr, rb, jx, jy);
+}
+
 // Pre-collision populations of both colours of node (x, y) at time t in FP64
 // (boundary conditions included), for state export.
 template <bool HERMITE, class Loader>
@@ -530,8 +618,8 @@ __device__ __forceinline__ void pull_populations(const Phys &p, const Loader &ld
     double sr = 0.0, sb = 0.0;
 #pragma unroll
     for (int i = 1; i < 9; i++) {
-        const bool bounce = (CY(i) > 0 && bottom) || (CY(i) < 0 && top);
-        const int xs = bounce ? x : x - CX(i), ys = bounce ? y : y - CY(i), ii = bounce ? OPP(i) : i;
+        const Link lk = link_of<LINKS_ALL>(p, ld.slip, i, x, y, bottom, top);
+        const int xs = lk.xs, ys = lk.ys, ii = lk.ii;
         nr[i] = (double)p.phi_r[C2(i)] * ld.rho(0, xs, ys) + ld.dev(0, ii, xs, ys);
         nb[i] = (double)p.phi_b[C2(i)] * ld.rho(1, xs, ys) + ld.dev(1, ii, xs, ys);
         sr += ld.dev(0, i, x, y);

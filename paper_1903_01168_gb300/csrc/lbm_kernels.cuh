@@ -31,6 +31,7 @@ struct GlobalLoader {
     const T *dev0;       // &dev[b][0][0][0]
     long long rho_plane, dev_plane, rho_row, dev_row;
     int ny;
+    int slip;   // free-slip walls
     SplitC q;
     __device__ __forceinline__ GlobalLoader(const SimDesc &d, int b) {
         rho0 = d.rho + b * d.rho_buf + d.ghost;
@@ -40,6 +41,7 @@ struct GlobalLoader {
         rho_row = d.rho_row;
         dev_row = d.dev_row;
         ny = d.ph.ny;
+        slip = d.wet.slip;
         q = split_consts(d.ph);
     }
     __device__ __forceinline__ int wrap(int ys) const { return ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys); }
@@ -76,6 +78,7 @@ struct SmemLoader {
     const unsigned char *r0, *r1, *r2;
     int y, x0;
     SplitC q;
+    static constexpr int slip = 0;   // the fused kernel runs no free-slip lattices
     __device__ __forceinline__ const unsigned char *row(int ys) const {
         const int dy = ys - y;
         return dy < 0 ? r0 : (dy == 0 ? r1 : r2);
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
                     const int X = x0 - 1 + c;
                     const float ps = wall_psi(p, X, [&](int Xp) {
                         float rr, rb, jx, jy;
-                        pull_moments<HERMITE, false>(p, L, Xp, Yn, t, rr, rb, jx, jy);
+                        pull_moments_rows<HERMITE, false, LINKS_NOSLIP>(p, L, Xp, Yn, t, rr, rb, jx, jy);
                         return colour_field(p, rr, rb);
                     });
                     ring_psi[rs + c] = ps;
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
                     const int c = tid + 1;
                     const int X = x0 + tid;
                     Pulled P;
-                    pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                    pull_node_rows<HERMITE, LINKS_NOSLIP>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
                     ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
                     out = P;
                     if (HERMITE_SRC) {
@@ -371,7 +374,7 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
                     int X = x0 - 1 + c;
                     if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
                     Pulled P;
-                    pull_node<HERMITE>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                    pull_node_rows<HERMITE, LINKS_NOSLIP>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
                     ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
                     if (HERMITE_SRC) {
                         const NodeMoments m = node_moments(p, P);
@@ -530,6 +533,7 @@ __global__ void k_tp_collide(const SimDesc *__restrict__ dp, int step_offset, co
         pull_node<HERMITE>(p, L, x, y, t, true, aux[n + k], aux[2 * n + k], P);
         float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
         s2i4([&](int dx, int dy) { return aux_at(p, aux, x + dx, y + dy, true); }, Fx, Fy);
+        contact_angle_adjust(d.wet, p, y, Fx, Fy);
         if (HERMITE_SRC) {
             float gx_, gy_;
             s2i4([&](int dx, int dy) { return aux_at(p, aux + 3 * n, x + dx, y + dy, false); }, dQx, gy_);
@@ -580,11 +584,21 @@ __global__ void k_init(const SimDesc *__restrict__ dp, const double *__restrict_
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             int X = x + CX(i), Y = y + CY(i);
-            int mode = 0;   // 0: read by node (X, Y), 1: bounced back to (x, y), 2: unread
+            // 0: read by node (X, Y), 1: bounced back to (x, y), 2: unread,
+            // 3: sent on along a free-slip wall to node (X, y) in direction MIRY(i)
+            int mode = 0;
             if (i != 0) {
                 if (Y < 0 || Y >= ny) {
-                    if (p.bc_y == BC_WALL) mode = 1;
-                    else Y = Y < 0 ? Y + ny : Y - ny;
+                    if (p.bc_y == BC_WALL) {
+                        mode = 1;
+                        if (d.wet.slip && (p.bc_x == BC_PERIODIC || (X >= 0 && X < nx))) {
+                            mode = 3;
+                            Y = y;
+                            X = X < 0 ? X + nx : (X >= nx ? X - nx : X);
+                        }
+                    } else {
+                        Y = Y < 0 ? Y + ny : Y - ny;
+                    }
                 }
                 if (mode == 0 && (X < 0 || X >= nx)) {
                     if (p.bc_x == BC_PERIODIC) X = X < 0 ? X + nx : X - nx;
@@ -593,6 +607,7 @@ __global__ void k_init(const SimDesc *__restrict__ dp, const double *__restrict_
             }
             for (int kk = 0; kk < 2; kk++) {
                 if (mode == 0) v[kk][i] = feq(kk, i, X, Y);
+                else if (mode == 3) v[kk][i] = feq(kk, MIRY(i), X, Y);
                 else if (mode == 1) v[kk][i] = feq(kk, OPP(i), x, y);
                 else v[kk][i] = pops ? pops[(long long)(kk * 9 + i) * n + k]
                                      : (double)phi_k(p, kk, C2(i)) * (kk == 0 ? rr[k] : rb[k]);

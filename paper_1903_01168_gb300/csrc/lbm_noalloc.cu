@@ -93,6 +93,7 @@ __global__ void k_na_collide(const __grid_constant__ SimDesc d, int step_offset,
         pull_node<HERMITE>(p, L, x, y, t, true, aux[n + k], aux[2 * n + k], P);
         float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
         s2i4([&](int dx, int dy) { return aux_at(p, aux, x + dx, y + dy, true); }, Fx, Fy);
+        contact_angle_adjust(d.wet, p, y, Fx, Fy);
         if (HERMITE_SRC) {
             float gx_, gy_;
             s2i4([&](int dx, int dy) { return aux_at(p, aux + 3 * n, x + dx, y + dy, false); }, dQx, gy_);

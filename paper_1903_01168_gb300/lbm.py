@@ -65,6 +65,7 @@ class lbm_params(ctypes.Structure):
         ("inlet_mode", ctypes.c_int), ("inlet_period_r", ctypes.c_int),
         ("inlet_period_b", ctypes.c_int), ("inlet_layer", ctypes.c_int),
         ("kernel", ctypes.c_int), ("plan_rows", ctypes.c_int), ("plan", ctypes.c_int),
+        ("wall_slip", ctypes.c_int), ("contact_angle", ctypes.c_double),
     ]
 
 
