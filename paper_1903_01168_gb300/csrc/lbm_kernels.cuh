@@ -152,10 +152,20 @@ __device__ __forceinline__ void pull_rho_coop16(const Phys &p, const Loader &ld,
     const int c2 = cx * cx + cy * cy;
     const float ph = k == 0 ? (c2 == 1 ? p.phi_r[1] : p.phi_r[2]) : (c2 == 1 ? p.phi_b[1] : p.phi_b[2]);
     const float own = ld.rho_rt(k, x, y);
-    float v = ph * (ld.rho_rt(k, x - cx, y - cy) - own) + (ld.dev_rt(k, i, x - cx, y - cy) - ld.dev_rt(k, i, x, y));
+    float v;
+    if (Loader::SPLIT) {
+        // split form: residual difference plus the source's shift; the node's own
+        // shifts sum to 4 m (dphi_1 + dphi_2), taken off once after the reduction
+        const float sg = k == 0 ? 1.0f : -1.0f;
+        v = ph * (ld.rho_rt(k, x - cx, y - cy) - own) + (ld.res(k, i, x - cx, y - cy) - ld.res(k, i, x, y)) +
+            sg * ld.shift(i, x - cx, y - cy);
+    } else {
+        v = ph * (ld.rho_rt(k, x - cx, y - cy) - own) + (ld.dev_rt(k, i, x - cx, y - cy) - ld.dev_rt(k, i, x, y));
+    }
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     v += __shfl_xor_sync(0xffffffffu, v, 2);
     v += __shfl_xor_sync(0xffffffffu, v, 4);
+    if (Loader::SPLIT) v -= (k == 0 ? 1.0f : -1.0f) * ld.own_shift_sum(x, y);
     const float mine = own + v;                        // colour k's new density
     const float other = __shfl_xor_sync(0xffffffffu, mine, 8);
     rr = k == 0 ? mine : other;
