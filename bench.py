@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic of one k_step_fused launch on this workload from an ncu capture
 # (profiles/k_step_fused_laplace_sweep_40x256.md), valid only for the kernel
 # sources with this hash; reported as null otherwise.
-NCU_TRAFFIC = {"sources_sha": "b7545e8620bd3d66", "bytes_per_launch": 222819328 + 155762944}
+NCU_TRAFFIC = {"sources_sha": "53264e91f9e3623d", "bytes_per_launch": 222819328 + 155179520}
 
 
 def kernel_sources_sha() -> str:
