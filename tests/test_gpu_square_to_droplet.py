@@ -3,10 +3,10 @@
 (1, 100), each run for 10 t_sigma.  At 60 x 60 the GPU's error equals the
 oracle's; every pressure inside a drop is within 10 % of Laplace's jump, and for
 (1, 1) the error at 200 is below the one at 60.  The
-measured orders of convergence are printed beside the paper's (0.718 for (1, 1),
-1.577 for (5, 2); its (1, 100) order is not printed legibly here) and recorded in
-the design notes, not pinned: the paper gives no viscosities, steady-state time
-or exact norm."""
+measured orders of convergence are printed beside the paper's LBM "bubble only"
+orders (0.718 for (1, 1), 1.577 for (5, 2), 1.604 for (1, 100)) and recorded in the
+design notes, not pinned: the paper gives no viscosities, steady-state time or
+exact norm."""
 import math
 
 import numpy as np
