@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the
 same seeded inputs, plus bit-level consistency of the GPU paths among themselves.
 
-Tolerances (spec: relative L-infinity 1e-5 on rho and u after 100 FP32 steps):
+Tolerances (the parity bar: relative L-infinity 1e-5 on rho and u after 100 FP32 steps):
   rho : max_x |rho_gpu - rho_ora| / rho_ora                    <= 1e-5
   u   : max_x |u_gpu - u_ora| / max(||u_ora||_inf, U_ref)      <= 1e-5
 U_ref is the case's velocity scale (the imposed speed for flows; the capillary
