@@ -108,6 +108,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest value of x over all ranks (x itself without a process group):
+    every rank's timed region is bracketed by barriers, so the job takes as long
+    as its slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job MLUPS: every rank runs its own replica of the workload (weak
+    scaling), so the job updates world x nodes x steps nodes in `seconds`."""
+    return nodes_per_rank * steps * world / seconds / 1e6
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -310,12 +328,8 @@ def main():
         torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    t_max = ms
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    mlups = nodes * args.steps * world / (t_max * 1e-3) / 1e6
+    t_max = max_over_ranks(ms, dist)
+    mlups = job_mlups(nodes, args.steps, world, t_max * 1e-3)
     ms_per_step = t_max / args.steps
 
     # ---- end to end through the public API with host buffers
@@ -337,15 +351,11 @@ def main():
         batch.step(args.steps, use_graph=True)
         outs = [s.fields() for s in sims]
     torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    if dist is not None:
-        tt = torch.tensor([te], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+    te = max_over_ranks(time.perf_counter() - te0, dist)
     algo_bytes = BYTES_PER_UPDATE[storage] * nodes
     h2d = sum(4 * sp.nx * sp.ny * 8 for sp in specs)
     d2h = sum(5 * sp.nx * sp.ny * 8 for sp in specs)
-    e2e = {"value": nodes * args.steps * world / te / 1e6, "unit": "MLUPS",
+    e2e = {"value": job_mlups(nodes, args.steps, world, te), "unit": "MLUPS",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "upload of initial fields + K steps + download of final fields, per step"}
     assert all(np.isfinite(o["rho_r"]).all() for o in outs)
