@@ -68,3 +68,26 @@ def test_serving_trace_is_seeded_and_shaped_like_the_open_channel_case():
         assert 512 <= s.nx <= 8192 and 64 <= s.ny <= 256 and s.nx % 32 == 0 and s.ny % 32 == 0
         assert 5000 <= s.steps <= 50000 and s.storage in (0, 1, 2)
         assert s.bc_x == 2 and s.bc_y == 1 and s.u_in_r > 0 and s.u_in_b > 0 and s.p_out > 0
+
+
+def test_chunk_length_runs_to_the_next_completion():
+    """Between admissions the server runs the batch to its next completion (at most
+    max_chunk steps); it checks back after `chunk` steps only while the next
+    request has yet to arrive (it may be admitted then), not while one that has
+    arrived is held back by the budget or the node cap."""
+    from types import SimpleNamespace as NS
+    from paper_1903_01168_gb300.serving import Server
+
+    srv = Server(budget_bytes=1e9, chunk=100, max_chunk=4000)
+
+    def member(steps, t):
+        return (NS(t=t), NS(spec=NS(steps=steps)), 0.0, 0)
+
+    active = {0: member(5000, 1000), 1: member(20000, 0)}
+    assert srv._chunk_len(active, deque(), now=1.0) == 4000                      # capped by max_chunk
+    active = {0: member(1500, 1000), 1: member(20000, 0)}
+    assert srv._chunk_len(active, deque(), now=1.0) == 500                       # next completion
+    future = deque([Request(7, 5.0, SimSpec(nx=8, ny=8))])
+    assert srv._chunk_len(active, future, now=1.0) == 100                        # an arrival is due
+    arrived = deque([Request(7, 0.5, SimSpec(nx=8, ny=8))])
+    assert srv._chunk_len(active, arrived, now=1.0) == 500                       # held back: run on
