@@ -27,6 +27,14 @@
  *     so that both pure phases at rest have the same pressure;
  *   - psi = +1 in pure red, as Eq. (eq:color_field) gives;
  *   - the Hermite factor "(3 c_i - 4)" is (3 |c_i|^2 - 4);
+ *   - the NS-recovery source: C^k_1 as printed, 3 (1 - s_1/2)(d_x Q_x + d_y Q_y);
+ *     C^k_7 = (1 - omega_eff/2)(d_x Q_x - d_y Q_y), not the printed
+ *     3 (1 - omega_eff/2)(d_x Q_x + d_y Q_y).  The Chapman-Enskog expansion fixes
+ *     both: Q^k_x is the excess of the D2Q9 third moment sum N c_x^3 over that
+ *     of a Maxwellian at (c_s^k)^2, and it enters e = sum (3|c|^2 - 4) N as
+ *     3 (d_x Q_x + d_y Q_y) but p_xx = sum (c_x^2 - c_y^2) N as d_x Q_x - d_y Q_y;
+ *     a source cancels an excess E of a moment relaxed at rate s when it is
+ *     (1 - s/2) E.  (c7_factor and c7_sign select the printed form);
  *   - A = 9 sigma omega_eff / 4 per node, from Eq. (eq:sigmaIsoAllen);
  *   - the perturbation term is added to each colour (two colours, one l != k
  *     term each), as Eq. (eq:perturbation) is printed;
@@ -288,7 +296,7 @@ void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double F
                 double dqx = k == 0 ? divQr_x : divQb_x;
                 double dqy = k == 0 ? divQr_y : divQb_y;
                 double C1 = 3.0 * (1.0 - 0.5 * s[1]) * (dqx + dqy);
-                double C7 = 3.0 * (1.0 - 0.5 * w) * (dqx + p->c7_sign * dqy);
+                double C7 = p->c7_factor * (1.0 - 0.5 * w) * (dqx + p->c7_sign * dqy);
                 t[1] -= C1;
                 t[7] -= C7;
             }

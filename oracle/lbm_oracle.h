@@ -42,7 +42,8 @@ typedef struct {
     int collision;      /* ORC_BGK / ORC_MRT */
     int equilibrium;    /* ORC_EQ_STD / ORC_EQ_HERMITE (Hermite adds U^k under MRT) */
     double mrt_lambda;  /* s_0..s_6 = lambda * omega_eff */
-    double c7_sign;     /* sign of d_y Q_y inside C^k_7 (+1 as printed) */
+    double c7_sign;     /* sign of d_y Q_y inside C^k_7 (-1 derived; +1 as printed) */
+    double c7_factor;   /* factor of C^k_7 (1 derived; 3 as printed) */
     int perturb_mode;   /* ORC_PERTURB_PER_COLOUR (as printed) or ORC_PERTURB_ONCE */
     int bc_x, bc_y;     /* ORC_PERIODIC / ORC_WALL / ORC_INOUT (x only) */
     double u_in_r, u_in_b; /* inlet speeds of the red / blue phase */

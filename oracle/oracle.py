@@ -37,7 +37,7 @@ class _Params(ctypes.Structure):
         ("beta", ctypes.c_double), ("gx", ctypes.c_double), ("gy", ctypes.c_double),
         ("collision", ctypes.c_int), ("equilibrium", ctypes.c_int),
         ("mrt_lambda", ctypes.c_double), ("c7_sign", ctypes.c_double),
-        ("perturb_mode", ctypes.c_int),
+        ("c7_factor", ctypes.c_double), ("perturb_mode", ctypes.c_int),
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("u_in_r", ctypes.c_double), ("u_in_b", ctypes.c_double), ("p_out", ctypes.c_double),
         ("inlet_mode", ctypes.c_int), ("inlet_period_r", ctypes.c_int),
@@ -64,7 +64,8 @@ class OracleParams:
     collision: int = BGK
     equilibrium: int = EQ_STD
     mrt_lambda: float = 0.8
-    c7_sign: float = 1.0
+    c7_sign: float = -1.0
+    c7_factor: float = 1.0
     perturb_mode: int = PERTURB_PER_COLOUR
     bc_x: int = PERIODIC
     bc_y: int = PERIODIC
@@ -93,39 +94,57 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def bind(path: str) -> ctypes.CDLL:
+    """Load an oracle shared library and declare its C signatures."""
+    L = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    pp = ctypes.POINTER(_Params)
+    L.orc_create.restype = ctypes.c_void_p
+    L.orc_create.argtypes = [pp]
+    L.orc_destroy.argtypes = [ctypes.c_void_p]
+    L.orc_time.restype = ctypes.c_long
+    L.orc_time.argtypes = [ctypes.c_void_p]
+    L.orc_set_pops.argtypes = [ctypes.c_void_p, dp]
+    L.orc_get_pops.argtypes = [ctypes.c_void_p, dp]
+    L.orc_init_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
+    L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    L.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
+    L.orc_gradient_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
+    L.orc_derived.argtypes = [pp] + [dp] * 8
+    L.orc_equilibrium.argtypes = [pp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, dp]
+    L.orc_omega_eff.restype = ctypes.c_double
+    L.orc_omega_eff.argtypes = [pp, ctypes.c_double]
+    L.orc_perturbation.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_recolour.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, dp, dp, dp]
+    L.orc_mrt_matrices.argtypes = [dp, dp]
+    L.orc_collide_node.argtypes = [pp, dp, ctypes.c_double, ctypes.c_double] + \
+        [ctypes.c_double] * 4 + [dp]
+    L.orc_zouhe_inlet.argtypes = [pp, ctypes.c_double, dp, dp]
+    L.orc_zouhe_outlet.argtypes = [pp, dp, dp]
+    return L
+
+
+def compile_variant(source_text: str, out_dir: str) -> str:
+    """Compile a modified copy of the oracle source (the tests plant mistakes in
+    it to show that the pins catch them) into out_dir; returns the library path."""
+    src = os.path.join(out_dir, "lbm_oracle_variant.c")
+    with open(src, "w") as f:
+        f.write(source_text)
+    so = os.path.join(out_dir, "liblbm_oracle_variant.so")
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-I", _HERE, "-o", so, src,
+                           "-lm"])
+    return so
+
+
 _lib = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
-        dp = ctypes.POINTER(ctypes.c_double)
-        pp = ctypes.POINTER(_Params)
-        L.orc_create.restype = ctypes.c_void_p
-        L.orc_create.argtypes = [pp]
-        L.orc_destroy.argtypes = [ctypes.c_void_p]
-        L.orc_time.restype = ctypes.c_long
-        L.orc_time.argtypes = [ctypes.c_void_p]
-        L.orc_set_pops.argtypes = [ctypes.c_void_p, dp]
-        L.orc_get_pops.argtypes = [ctypes.c_void_p, dp]
-        L.orc_init_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
-        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
-        L.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
-        L.orc_derived.argtypes = [pp] + [dp] * 8
-        L.orc_equilibrium.argtypes = [pp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                      ctypes.c_double, dp]
-        L.orc_omega_eff.restype = ctypes.c_double
-        L.orc_omega_eff.argtypes = [pp, ctypes.c_double]
-        L.orc_perturbation.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
-        L.orc_recolour.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double, dp, dp, dp]
-        L.orc_mrt_matrices.argtypes = [dp, dp]
-        L.orc_collide_node.argtypes = [pp, dp, ctypes.c_double, ctypes.c_double] + \
-            [ctypes.c_double] * 4 + [dp]
-        L.orc_zouhe_inlet.argtypes = [pp, ctypes.c_double, dp, dp]
-        L.orc_zouhe_outlet.argtypes = [pp, dp, dp]
-        _lib = L
+        _lib = bind(build())
     return _lib
 
 
@@ -145,12 +164,13 @@ class Oracle:
     def __init__(self, params: OracleParams):
         self.params = params
         self._cp = params.to_c()
-        self._h = lib().orc_create(ctypes.byref(self._cp))
+        self._L = lib()
+        self._h = self._L.orc_create(ctypes.byref(self._cp))
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            lib().orc_destroy(h)
+            self._L.orc_destroy(h)
             self._h = None
 
     @property
@@ -159,28 +179,28 @@ class Oracle:
 
     @property
     def t(self) -> int:
-        return lib().orc_time(self._h)
+        return self._L.orc_time(self._h)
 
     def init_fields(self, rho_r, rho_b, ux, uy):
         a = [_f64(v).reshape(self.shape) for v in (rho_r, rho_b, ux, uy)]
-        lib().orc_init_fields(self._h, *[_ptr(v) for v in a])
+        self._L.orc_init_fields(self._h, *[_ptr(v) for v in a])
 
     def set_pops(self, pops):
         a = _f64(pops).reshape((2, 9) + self.shape)
-        lib().orc_set_pops(self._h, _ptr(a))
+        self._L.orc_set_pops(self._h, _ptr(a))
 
     def get_pops(self) -> np.ndarray:
         out = np.empty((2, 9) + self.shape)
-        lib().orc_get_pops(self._h, _ptr(out))
+        self._L.orc_get_pops(self._h, _ptr(out))
         return out
 
     def step(self, n: int = 1):
-        lib().orc_step(self._h, int(n))
+        self._L.orc_step(self._h, int(n))
 
     def fields(self) -> dict:
         names = ("rho_r", "rho_b", "ux", "uy", "p", "psi")
         out = {k: np.empty(self.shape) for k in names}
-        lib().orc_fields(self._h, *[_ptr(out[k]) for k in names])
+        self._L.orc_fields(self._h, *[_ptr(out[k]) for k in names])
         return out
 
 
@@ -253,7 +273,5 @@ def gradient_fields(o: Oracle):
     """Colour gradient F and the S2I4 derivatives of Q^k for every node."""
     ny, nx = o.shape
     Fx, Fy, dQ = np.empty(o.shape), np.empty(o.shape), np.empty((4, ny, nx))
-    L = lib()
-    L.orc_gradient_fields.argtypes = [ctypes.c_void_p] + [ctypes.POINTER(ctypes.c_double)] * 3
-    L.orc_gradient_fields(o._h, _ptr(Fx), _ptr(Fy), _ptr(dQ))
+    o._L.orc_gradient_fields(o._h, _ptr(Fx), _ptr(Fy), _ptr(dQ))
     return Fx, Fy, dQ
