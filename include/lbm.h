@@ -90,7 +90,9 @@ typedef struct {
     double gamma;        /* density ratio rho_r^0 / rho_b^0 >= 1 (Eq. (eq:gammaAlphaBeta)) */
     double alpha_b;      /* rest fraction of blue, 0 < alpha_b < 1 (paper: 0.2); alpha_r =
                             1 - (1 - alpha_b)/gamma */
-    double tau_r, tau_b; /* relaxation times, omega_k = 1/tau_k, tau_k = 3 nu_k + 1/2 */
+    double tau_r, tau_b; /* relaxation times, omega_k = 1/tau_k; kinematic viscosity
+                            nu_k = (tau_k - 1/2)/3 with the standard equilibrium (Sec. 2.1),
+                            nu_k = (c_s^k)^2 (tau_k - 1/2) with the Hermite one */
     double delta;        /* omega_eff interpolation half-width (paper: 0.1) */
     double sigma;        /* surface tension (lattice units) */
     double beta;         /* recolouring parameter in [0, 1] (paper default 0.99) */
@@ -98,7 +100,11 @@ typedef struct {
     int collision;       /* lbm_collision */
     int equilibrium;     /* lbm_equilibrium; HERMITE adds U^k when collision == MRT */
     double mrt_lambda;   /* s_0..s_6 = lambda omega_eff, s_7 = s_8 = omega_eff (paper: 4/5) */
-    double c7_sign;      /* sign of the d_y Q_y term of C^k_7 (+1 as printed) */
+    double c7_sign;      /* sign of the d_y Q_y term of C^k_7: -1 (default) from the
+                            Chapman-Enskog expansion, +1 as the paper prints it */
+    double c7_factor;    /* factor of C^k_7: 1 (default) from the expansion, 3 as printed.
+                            C^k_7 = c7_factor (1 - omega_eff/2)(d_x Q_x + c7_sign d_y Q_y)
+                            (Sec. 2.1, "Proper recovery of Navier-Stokes equations") */
     int bc_x;            /* LBM_BC_PERIODIC or LBM_BC_INOUT */
     int bc_y;            /* LBM_BC_PERIODIC or LBM_BC_WALL */
     int storage;         /* lbm_storage */
@@ -142,6 +148,31 @@ typedef struct {
     double dp;            /* p_in - p_out (Laplace pressure jump) */
     long long nonfinite;  /* nodes with a non-finite density or velocity */
 } lbm_diag;
+
+/* Geometry of a train of light bubbles moving along x (the slug measurements of
+ * Sec. 5.1: bubble and slug lengths, the liquid film between a bubble and the
+ * walls, the bubble nose).  Measured on the colour field psi of the state:
+ *   - the centreline profile psi_c(x): psi on the middle row, or the mean of the
+ *     two middle rows when ny is even, taken linear between nodes;
+ *   - a bubble's tail is a centreline zero of psi_c where it goes from >= 0
+ *     (heavy) to < 0 (light) in +x, its nose the next zero from < 0 to >= 0;
+ *   - the light thickness of a column, g(x) = sum_y (1 - psi(x, y)) / 2, taken
+ *     linear between columns; a bubble's film thickness is (ny - g(x_mid)) / 2 at
+ *     its middle x_mid = (tail + nose) / 2.
+ * Periodic x closes the line (a bubble may straddle x = 0); on an open x axis
+ * only bubbles with both ends inside count, and a slug needs a bubble on both
+ * sides. */
+#define LBM_SLUG_MAX 16
+typedef struct {
+    long long t;          /* time step of the state */
+    int n_bubbles;        /* bubbles cut by the centreline (all of them count in the
+                             means; the first LBM_SLUG_MAX are listed) */
+    int n_slugs;          /* liquid slugs between two counted bubbles */
+    double bubble_len;    /* mean bubble length nose - tail on the centreline */
+    double slug_len;      /* mean slug length (next tail - nose) on the centreline */
+    double film;          /* mean film thickness at the bubbles' middles */
+    double x_tail[LBM_SLUG_MAX], x_nose[LBM_SLUG_MAX]; /* in [0, nx), ordered in x by tail */
+} lbm_slug;
 
 typedef struct lbm_sim lbm_sim;
 typedef struct lbm_batch lbm_batch;
@@ -218,6 +249,12 @@ lbm_status lbm_read_populations(lbm_sim *s, double *pops);
  * filled) if any node is non-finite.  Synchronous. */
 lbm_status lbm_diagnostics(lbm_sim *s, lbm_diag *out);
 
+/* Slug-train geometry of the current state (lbm_slug above), computed from an
+ * FP64 per-column profile that a kernel reduces on the device.  gas: NULL, or a
+ * caller-owned host array of nx doubles that receives g(x) (the light thickness
+ * of each column; behind a nose, g(x_nose - s) is the nose shape).  Synchronous. */
+lbm_status lbm_slug_geometry(lbm_sim *s, lbm_slug *out, double *gas);
+
 /* Raw state (both population buffers and the time step): size, save to a
  * host buffer, restore from one.  Synchronous.  A restored state continues
  * bit-identically. */
@@ -248,14 +285,21 @@ void lbm_destroy(lbm_sim *s);
  *                advanced in place (the state at t + n ends in the same buffer)
  *   t            time step of the state in `state`
  *   cuda_stream  stream the kernels are queued on (asynchronous)
- * The intermediate colour-field pass uses a static scratch array of 5 MiB that
- * every GPU loading the library holds until exit.  Its device address is looked
- * up by the first call made on each device, with that device current; make that
- * first call before capturing any stream.  All calls share that one scratch and
- * it keeps the previous call's contents: calls that may overlap on the GPU
- * (different streams, or different simulations on one stream that are not
- * ordered) race, so order them.  Lattices above 262144 nodes are rejected with
- * LBM_EINVAL and a message in lbm_last_error(NULL). */
+ * The intermediate colour-field pass uses a static scratch array of 5 MiB, and
+ * the kernels read the simulation's descriptor from a static slot beside it;
+ * every GPU loading the library holds both until exit.  Their device addresses
+ * are looked up by the first call made on each device, with that device
+ * current; make that first call before capturing any stream.  Each call copies
+ * the descriptor into its slot on `cuda_stream` (no allocation).  All calls
+ * share the scratch and the slot, which keep the previous call's contents:
+ * calls that may overlap on the GPU (different streams, or different
+ * simulations on one stream that are not ordered) race, so order them.
+ * Errors (message in lbm_last_error(NULL)):
+ *   LBM_EINVAL  invalid parameters, more than 262144 nodes, a state pointer that
+ *               is not device (or managed) memory of the current device, or a
+ *               misaligned state; LBM_ENOMEM  `bytes` too small;
+ *   LBM_ECUDA   a CUDA error left pending by earlier work (reported, and cleared,
+ *               before anything is queued), or a failed copy or launch. */
 lbm_status lbm_step_noalloc(const lbm_params *p, int nx, int ny, void *state, size_t bytes, long long t,
                             long n, void *cuda_stream);
 

@@ -18,6 +18,9 @@
  *   streaming + boundaries    Eq. (eq:subop4), Sec. 2.5 (bounce-back, periodic,
  *                             two-phase Zou-He inlet / outlet)
  *
+ * Rows are processed in parallel (OpenMP) where each node's update reads only
+ * the previous pass's arrays, so the result does not depend on the thread count.
+ *
  * Readings taken where the paper is silent, garbled or self-contradictory
  * (each is listed in the design notes of the repository):
  *   - direction order is the standard one of the appendix matrices; every
@@ -52,9 +55,14 @@
  */
 #include "lbm_oracle.h"
 
-#include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#include <tgmath.h>
+
+/* The arithmetic type (FP64 unless the header's ORC_REAL is overridden); the
+ * parameters are read through (real) casts so that an FP32 build computes in
+ * FP32 throughout. */
+typedef orc_real real;
 
 /* ---------------------------------------------------------------- lattice */
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -68,70 +76,70 @@ static const int MIRX[9] = {0, 3, 2, 1, 4, 6, 5, 8, 7};
 static int c2(int i) { return CX[i] * CX[i] + CY[i] * CY[i]; }
 
 /* D2Q9 weights W_i (Sec. 2.1). */
-static double W(int i) {
+static real W(int i) {
     int n = c2(i);
     return n == 0 ? 4.0 / 9.0 : (n == 1 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
 /* Rest weights phi^k_i of the density-ratio equilibrium (Sec. 2.1). */
-static double phi(double alpha, int i) {
+static real phi(real alpha, int i) {
     int n = c2(i);
     return n == 0 ? alpha : (n == 1 ? (1.0 - alpha) / 5.0 : (1.0 - alpha) / 20.0);
 }
 
 /* S2I4 gradient weights xi_i, Eq. (eq:colorGradient). */
-static double xi(int i) {
+static real xi(int i) {
     int n = c2(i);
     return n == 0 ? 0.0 : (n == 1 ? 1.0 / 3.0 : 1.0 / 12.0);
 }
 
 /* Perturbation constants B_i, Eq. (eq:perturbation). */
-static double Bc(int i) {
+static real Bc(int i) {
     int n = c2(i);
     return n == 0 ? -4.0 / 27.0 : (n == 1 ? 2.0 / 27.0 : 5.0 / 108.0);
 }
 
 /* ------------------------------------------------------------- parameters */
-void orc_derived(const orc_params *p, double *alpha_r, double *omega_r, double *omega_b,
-                 double *chi, double *eta, double *kappa, double *lam, double *nu) {
-    double ar = 1.0 - (1.0 - p->alpha_b) / p->gamma;    /* Eq. (eq:gammaAlphaBeta) */
-    double wr = 1.0 / p->tau_r, wb = 1.0 / p->tau_b;
-    double c = 2.0 * wr * wb / (wr + wb);
-    double e = 2.0 * (wr - c) / p->delta;
-    double l = 2.0 * (c - wb) / p->delta;
+void orc_derived(const orc_params *p, real *alpha_r, real *omega_r, real *omega_b,
+                 real *chi, real *eta, real *kappa, real *lam, real *nu) {
+    real ar = 1.0 - (1.0 - (real)p->alpha_b) / (real)p->gamma;    /* Eq. (eq:gammaAlphaBeta) */
+    real wr = 1.0 / (real)p->tau_r, wb = 1.0 / (real)p->tau_b;
+    real c = 2.0 * wr * wb / (wr + wb);
+    real e = 2.0 * (wr - c) / (real)p->delta;
+    real l = 2.0 * (c - wb) / (real)p->delta;
     if (alpha_r) *alpha_r = ar;
     if (omega_r) *omega_r = wr;
     if (omega_b) *omega_b = wb;
     if (chi) *chi = c;
     if (eta) *eta = e;
-    if (kappa) *kappa = -e / (2.0 * p->delta);
+    if (kappa) *kappa = -e / (2.0 * (real)p->delta);
     if (lam) *lam = l;
-    if (nu) *nu = l / (2.0 * p->delta);
+    if (nu) *nu = l / (2.0 * (real)p->delta);
 }
 
-static double alpha_of(const orc_params *p, int k) {
-    double ar;
+static real alpha_of(const orc_params *p, int k) {
+    real ar;
     orc_derived(p, &ar, 0, 0, 0, 0, 0, 0, 0);
-    return k == 0 ? ar : p->alpha_b;
+    return k == 0 ? ar : (real)p->alpha_b;
 }
 
-static double rho0_of(const orc_params *p, int k) { return k == 0 ? p->gamma : 1.0; }
+static real rho0_of(const orc_params *p, int k) { return k == 0 ? (real)p->gamma : 1.0; }
 
 /* (c_s^k)^2 = 3 (1 - alpha_k) / 5, Eq. (eq:pressureRelation). */
-static double cs2_of(const orc_params *p, int k) { return 3.0 * (1.0 - alpha_of(p, k)) / 5.0; }
+static real cs2_of(const orc_params *p, int k) { return 3.0 * (1.0 - alpha_of(p, k)) / 5.0; }
 
 /* --------------------------------------------------------------- operators */
 
 /* Eq. (eq:equilibrium), or Eq. (eq:equilibrium_hermite) with the factor read
  * as (3|c_i|^2 - 4). */
-void orc_equilibrium(const orc_params *p, int k, double rho_k, double ux, double uy,
-                     double *neq) {
-    double alpha = alpha_of(p, k);
-    double cs2 = cs2_of(p, k);
-    double usq = ux * ux + uy * uy;
+void orc_equilibrium(const orc_params *p, int k, real rho_k, real ux, real uy,
+                     real *neq) {
+    real alpha = alpha_of(p, k);
+    real cs2 = cs2_of(p, k);
+    real usq = ux * ux + uy * uy;
     for (int i = 0; i < 9; i++) {
-        double cu = CX[i] * ux + CY[i] * uy;
-        double lin = 3.0 * cu;
+        real cu = CX[i] * ux + CY[i] * uy;
+        real lin = 3.0 * cu;
         if (p->equilibrium == ORC_EQ_HERMITE)
             lin = 3.0 * cu * (1.0 + 0.5 * (3.0 * cs2 - 1.0) * (3.0 * c2(i) - 4.0));
         neq[i] = rho_k * phi(alpha, i) + rho_k * W(i) * (lin + 4.5 * cu * cu - 1.5 * usq);
@@ -139,27 +147,27 @@ void orc_equilibrium(const orc_params *p, int k, double rho_k, double ux, double
 }
 
 /* Piecewise omega_eff(psi) of Sec. 2.1, with f_r and f_b as printed. */
-double orc_omega_eff(const orc_params *p, double psi) {
-    double wr, wb, chi, eta, kappa, lam, nu;
+real orc_omega_eff(const orc_params *p, real psi) {
+    real wr, wb, chi, eta, kappa, lam, nu;
     orc_derived(p, 0, &wr, &wb, &chi, &eta, &kappa, &lam, &nu);
-    if (psi > p->delta) return wr;
+    if (psi > (real)p->delta) return wr;
     if (psi > 0.0) return chi + eta * psi + kappa * psi * psi;
-    if (psi >= -p->delta) return chi + lam * psi + nu * psi * psi;
+    if (psi >= -(real)p->delta) return chi + lam * psi + nu * psi * psi;
     return wb;
 }
 
 /* One colour's increment (A/2)|F| [W_i (F.c_i)^2/|F|^2 - B_i], Eq. (eq:perturbation).
  * Zero when |F| == 0. */
-void orc_perturbation(const orc_params *p, double A, double Fx, double Fy, double *dN) {
+void orc_perturbation(const orc_params *p, real A, real Fx, real Fy, real *dN) {
     (void)p;
-    double F2 = Fx * Fx + Fy * Fy;
+    real F2 = Fx * Fx + Fy * Fy;
     for (int i = 0; i < 9; i++) {
         if (F2 == 0.0) {
             dN[i] = 0.0;
             continue;
         }
-        double Fn = sqrt(F2);
-        double Fc = Fx * CX[i] + Fy * CY[i];
+        real Fn = sqrt(F2);
+        real Fc = Fx * CX[i] + Fy * CY[i];
         dN[i] = 0.5 * A * Fn * (W(i) * Fc * Fc / F2 - Bc(i));
     }
 }
@@ -167,17 +175,17 @@ void orc_perturbation(const orc_params *p, double A, double Fx, double Fy, doubl
 /* Eq. (eq:recoloringOperator): N^r_i = rho_r/rho N_i + beta rho_r rho_b/rho^2 cos(phi_i)
  * sum_k N^{k(e)}_i(rho_k, 0, alpha_k); N^b_i = N_i - N^r_i.  The second term is
  * zero for i = 0 or |F| == 0. */
-void orc_recolour(const orc_params *p, double rho_r, double rho_b, double Fx, double Fy,
-                  const double *N, double *Nr, double *Nb) {
-    double rho = rho_r + rho_b;
-    double F2 = Fx * Fx + Fy * Fy;
-    double ar = alpha_of(p, 0), ab = alpha_of(p, 1);
+void orc_recolour(const orc_params *p, real rho_r, real rho_b, real Fx, real Fy,
+                  const real *N, real *Nr, real *Nb) {
+    real rho = rho_r + rho_b;
+    real F2 = Fx * Fx + Fy * Fy;
+    real ar = alpha_of(p, 0), ab = alpha_of(p, 1);
     for (int i = 0; i < 9; i++) {
-        double term = 0.0;
+        real term = 0.0;
         if (i != 0 && F2 != 0.0) {
-            double cosphi = (CX[i] * Fx + CY[i] * Fy) / (sqrt((double)c2(i)) * sqrt(F2));
-            double rest = rho_r * phi(ar, i) + rho_b * phi(ab, i); /* N^{k(e)}(rho_k, 0) summed */
-            term = p->beta * rho_r * rho_b / (rho * rho) * cosphi * rest;
+            real cosphi = (CX[i] * Fx + CY[i] * Fy) / (sqrt((real)c2(i)) * sqrt(F2));
+            real rest = rho_r * phi(ar, i) + rho_b * phi(ab, i); /* N^{k(e)}(rho_k, 0) summed */
+            term = (real)p->beta * rho_r * rho_b / (rho * rho) * cosphi * rest;
         }
         Nr[i] = rho_r / rho * N[i] + term;
         Nb[i] = rho_b / rho * N[i] - term;
@@ -206,41 +214,41 @@ static const int MINV36[9][9] = {
     {4, 2, 1, -6, -3, -6, -3, 0, 9},
     {4, 2, 1, 6, 3, -6, -3, 0, -9}};
 
-void orc_mrt_matrices(double *M, double *Minv) {
+void orc_mrt_matrices(real *M, real *Minv) {
     for (int a = 0; a < 9; a++)
         for (int b = 0; b < 9; b++) {
-            M[a * 9 + b] = (double)M_INT[a][b];
-            Minv[a * 9 + b] = (double)MINV36[a][b] / 36.0;
+            M[a * 9 + b] = (real)M_INT[a][b];
+            Minv[a * 9 + b] = (real)MINV36[a][b] / 36.0;
         }
 }
 
-static void matvec(const double *A, const double *x, double *y) {
+static void matvec(const real *A, const real *x, real *y) {
     for (int a = 0; a < 9; a++) {
-        double s = 0.0;
+        real s = 0.0;
         for (int b = 0; b < 9; b++) s += A[a * 9 + b] * x[b];
         y[a] = s;
     }
 }
 
 /* Node moments: rho_k, rho, and u = (sum_k sum_i N^k_i c_i + rho g / 2) / rho. */
-static void node_moments(const orc_params *p, const double *Nk, double *rho_r, double *rho_b,
-                         double *ux, double *uy) {
-    double rr = 0.0, rb = 0.0, jx = 0.0, jy = 0.0;
+static void node_moments(const orc_params *p, const real *Nk, real *rho_r, real *rho_b,
+                         real *ux, real *uy) {
+    real rr = 0.0, rb = 0.0, jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; i++) {
         rr += Nk[i];
         rb += Nk[9 + i];
         jx += (Nk[i] + Nk[9 + i]) * CX[i];
         jy += (Nk[i] + Nk[9 + i]) * CY[i];
     }
-    double rho = rr + rb;
+    real rho = rr + rb;
     *rho_r = rr;
     *rho_b = rb;
-    *ux = (jx + 0.5 * rho * p->gx) / rho;
-    *uy = (jy + 0.5 * rho * p->gy) / rho;
+    *ux = (jx + 0.5 * rho * (real)p->gx) / rho;
+    *uy = (jy + 0.5 * rho * (real)p->gy) / rho;
 }
 
-static double colour_field(const orc_params *p, double rho_r, double rho_b) {
-    double a = rho_r / rho0_of(p, 0), b = rho_b / rho0_of(p, 1);
+static real colour_field(const orc_params *p, real rho_r, real rho_b) {
+    real a = rho_r / rho0_of(p, 0), b = rho_b / rho0_of(p, 1);
     return (a - b) / (a + b);                           /* Eq. (eq:color_field) */
 }
 
@@ -248,33 +256,33 @@ static double colour_field(const orc_params *p, double rho_r, double rho_b) {
  * the perturbation of each colour.  Input: pre-collision N^k_i of one node,
  * the colour gradient F and, for the Hermite/MRT source, the divergence parts
  * d_x Q^k_x and d_y Q^k_y of each colour. */
-void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double Fy,
-                      double divQr_x, double divQr_y, double divQb_x, double divQb_y,
-                      double *Nstar) {
-    double rho_r, rho_b, ux, uy;
+void orc_collide_node(const orc_params *p, const real *Nk, real Fx, real Fy,
+                      real divQr_x, real divQr_y, real divQb_x, real divQb_y,
+                      real *Nstar) {
+    real rho_r, rho_b, ux, uy;
     node_moments(p, Nk, &rho_r, &rho_b, &ux, &uy);
-    double psi = colour_field(p, rho_r, rho_b);
-    double w = orc_omega_eff(p, psi);
-    double A = 9.0 * p->sigma * w / 4.0;                /* Eq. (eq:sigmaIsoAllen) */
-    double M[81], Minv[81];
+    real psi = colour_field(p, rho_r, rho_b);
+    real w = orc_omega_eff(p, psi);
+    real A = 9.0 * (real)p->sigma * w / 4.0;                /* Eq. (eq:sigmaIsoAllen) */
+    real M[81], Minv[81];
     orc_mrt_matrices(M, Minv);
-    double s[9];
-    for (int a = 0; a < 9; a++) s[a] = p->mrt_lambda * w; /* s_0..s_6 */
+    real s[9];
+    for (int a = 0; a < 9; a++) s[a] = (real)p->mrt_lambda * w; /* s_0..s_6 */
     s[7] = w;
     s[8] = w;
 
     for (int k = 0; k < 2; k++) {
-        const double *N = Nk + 9 * k;
-        double *out = Nstar + 9 * k;
-        double rho_k = k == 0 ? rho_r : rho_b;
-        double neq[9];
+        const real *N = Nk + 9 * k;
+        real *out = Nstar + 9 * k;
+        real rho_k = k == 0 ? rho_r : rho_b;
+        real neq[9];
         orc_equilibrium(p, k, rho_k, ux, uy, neq);
 
         /* Guo source of colour k, force F^k = rho_k g. */
-        double fx = rho_k * p->gx, fy = rho_k * p->gy;
-        double src[9];
+        real fx = rho_k * (real)p->gx, fy = rho_k * (real)p->gy;
+        real src[9];
         for (int i = 0; i < 9; i++) {
-            double cu = CX[i] * ux + CY[i] * uy;
+            real cu = CX[i] * ux + CY[i] * uy;
             src[i] = W(i) * (3.0 * ((CX[i] - ux) * fx + (CY[i] - uy) * fy) +
                              9.0 * cu * (CX[i] * fx + CY[i] * fy));
         }
@@ -285,7 +293,7 @@ void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double F
                 out[i] = N[i] - w * (N[i] - neq[i]) + (1.0 - 0.5 * w) * src[i];
         } else {
             /* Eq. (eq:singleCollisionMRT): N - M^-1 S M (N - Neq) + M^-1 (I - S/2) M src + U^k */
-            double d[9], m[9], ms[9], t[9], back[9];
+            real d[9], m[9], ms[9], t[9], back[9];
             for (int i = 0; i < 9; i++) d[i] = N[i] - neq[i];
             matvec(M, d, m);
             matvec(M, src, ms);
@@ -293,10 +301,10 @@ void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double F
             if (p->equilibrium == ORC_EQ_HERMITE) {
                 /* C^k = [0, C_1, 0, 0, 0, 0, 0, C_7, 0]; U^k = M^-1 C^k is ADDED, so it
                  * enters t with a minus sign. */
-                double dqx = k == 0 ? divQr_x : divQb_x;
-                double dqy = k == 0 ? divQr_y : divQb_y;
-                double C1 = 3.0 * (1.0 - 0.5 * s[1]) * (dqx + dqy);
-                double C7 = p->c7_factor * (1.0 - 0.5 * w) * (dqx + p->c7_sign * dqy);
+                real dqx = k == 0 ? divQr_x : divQb_x;
+                real dqy = k == 0 ? divQr_y : divQb_y;
+                real C1 = 3.0 * (1.0 - 0.5 * s[1]) * (dqx + dqy);
+                real C7 = (real)p->c7_factor * (1.0 - 0.5 * w) * (dqx + (real)p->c7_sign * dqy);
                 t[1] -= C1;
                 t[7] -= C7;
             }
@@ -306,7 +314,7 @@ void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double F
 
         /* Eq. (eq:perturbation): one l != k term per colour. */
         if (p->perturb_mode == ORC_PERTURB_PER_COLOUR) {
-            double dN[9];
+            real dN[9];
             orc_perturbation(p, A, Fx, Fy, dN);
             for (int i = 0; i < 9; i++) out[i] += dN[i];
         }
@@ -314,7 +322,7 @@ void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double F
     if (p->perturb_mode == ORC_PERTURB_ONCE) {
         /* Alternative reading: one A/2 term on the colour-blind distribution
          * (put on the red set; only the colour-blind sum is used afterwards). */
-        double dN[9];
+        real dN[9];
         orc_perturbation(p, A, Fx, Fy, dN);
         for (int i = 0; i < 9; i++) Nstar[i] += dN[i];
     }
@@ -325,16 +333,16 @@ void orc_collide_node(const orc_params *p, const double *Nk, double Fx, double F
 /* West velocity inlet, the paper's north inlet rotated by +90 degrees.  On
  * entry Nr/Nb hold the post-streaming populations with the unknowns 1, 5, 8
  * undefined; f_r is the red fraction of the injected phase at this node. */
-void orc_zouhe_inlet(const orc_params *p, double f_r, double *Nr, double *Nb) {
-    double f_b = 1.0 - f_r;
-    double N[9];
+void orc_zouhe_inlet(const orc_params *p, real f_r, real *Nr, real *Nb) {
+    real f_b = 1.0 - f_r;
+    real N[9];
     for (int i = 0; i < 9; i++) N[i] = Nr[i] + Nb[i];
-    double Vx = f_r * p->u_in_r + f_b * p->u_in_b; /* v^in = v^{b,in} + v^{r,in} */
-    double Vy = 0.0;
-    double rho = (N[0] + N[2] + N[4] + 2.0 * (N[3] + N[6] + N[7])) / (1.0 - Vx);
-    double H = 0.0;
+    real Vx = f_r * (real)p->u_in_r + f_b * (real)p->u_in_b; /* v^in = v^{b,in} + v^{r,in} */
+    real Vy = 0.0;
+    real rho = (N[0] + N[2] + N[4] + 2.0 * (N[3] + N[6] + N[7])) / (1.0 - Vx);
+    real H = 0.0;
     if (p->equilibrium == ORC_EQ_HERMITE) {
-        double amix = f_r * (3.0 * cs2_of(p, 0) - 1.0) + f_b * (3.0 * cs2_of(p, 1) - 1.0);
+        real amix = f_r * (3.0 * cs2_of(p, 0) - 1.0) + f_b * (3.0 * cs2_of(p, 1) - 1.0);
         H = -rho * amix * Vx / 3.0;
     }
     N[1] = N[3] + 2.0 / 3.0 * rho * Vx + H;
@@ -349,22 +357,22 @@ void orc_zouhe_inlet(const orc_params *p, double f_r, double *Nr, double *Nb) {
 
 /* East pressure outlet, the paper's south outlet rotated by +90 degrees.
  * Unknowns 3, 6, 7.  The colour fraction comes from the known populations. */
-void orc_zouhe_outlet(const orc_params *p, double *Nr, double *Nb) {
+void orc_zouhe_outlet(const orc_params *p, real *Nr, real *Nb) {
     const int known[6] = {0, 1, 2, 4, 5, 8};
-    double kr = 0.0, kb = 0.0;
+    real kr = 0.0, kb = 0.0;
     for (int j = 0; j < 6; j++) {
         kr += Nr[known[j]];
         kb += Nb[known[j]];
     }
-    double psi = colour_field(p, kr, kb);
-    double f_r = 0.5 * (1.0 + psi), f_b = 1.0 - f_r;
-    double N[9];
+    real psi = colour_field(p, kr, kb);
+    real f_r = 0.5 * (1.0 + psi), f_b = 1.0 - f_r;
+    real N[9];
     for (int i = 0; i < 9; i++) N[i] = Nr[i] + Nb[i];
-    double rho = f_b * p->p_out / cs2_of(p, 1) + f_r * p->p_out / cs2_of(p, 0);
-    double Vx = -1.0 + (N[0] + N[2] + N[4] + 2.0 * (N[1] + N[5] + N[8])) / rho;
-    double H = 0.0;
+    real rho = f_b * (real)p->p_out / cs2_of(p, 1) + f_r * (real)p->p_out / cs2_of(p, 0);
+    real Vx = -1.0 + (N[0] + N[2] + N[4] + 2.0 * (N[1] + N[5] + N[8])) / rho;
+    real H = 0.0;
     if (p->equilibrium == ORC_EQ_HERMITE) {
-        double amix = f_r * (3.0 * cs2_of(p, 0) - 1.0) + f_b * (3.0 * cs2_of(p, 1) - 1.0);
+        real amix = f_r * (3.0 * cs2_of(p, 0) - 1.0) + f_b * (3.0 * cs2_of(p, 1) - 1.0);
         H = rho * amix * Vx / 3.0;
     }
     /* tangential outlet velocity is zero (v^out_x = 0 in the paper's frame) */
@@ -382,10 +390,10 @@ void orc_zouhe_outlet(const orc_params *p, double *Nr, double *Nb) {
 struct orc_sim {
     orc_params p;
     long t;
-    double *N;     /* pre-collision N^k_i(x, t) */
-    double *Npost; /* after collision, perturbation and recolouring */
-    double *rho_r, *rho_b, *ux, *uy, *psi;
-    double *Qx, *Qy; /* Q^k per colour: [k][y][x] */
+    real *N;     /* pre-collision N^k_i(x, t) */
+    real *Npost; /* after collision, perturbation and recolouring */
+    real *rho_r, *rho_b, *ux, *uy, *psi;
+    real *Qx, *Qy; /* Q^k per colour: [k][y][x] */
 };
 
 static size_t pidx(const orc_sim *s, int k, int i, int x, int y) {
@@ -396,15 +404,15 @@ orc_sim *orc_create(const orc_params *p) {
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
     s->p = *p;
     size_t n = (size_t)p->nx * p->ny;
-    s->N = (double *)calloc(18 * n, sizeof(double));
-    s->Npost = (double *)calloc(18 * n, sizeof(double));
-    s->rho_r = (double *)calloc(n, sizeof(double));
-    s->rho_b = (double *)calloc(n, sizeof(double));
-    s->ux = (double *)calloc(n, sizeof(double));
-    s->uy = (double *)calloc(n, sizeof(double));
-    s->psi = (double *)calloc(n, sizeof(double));
-    s->Qx = (double *)calloc(2 * n, sizeof(double));
-    s->Qy = (double *)calloc(2 * n, sizeof(double));
+    s->N = (real *)calloc(18 * n, sizeof(real));
+    s->Npost = (real *)calloc(18 * n, sizeof(real));
+    s->rho_r = (real *)calloc(n, sizeof(real));
+    s->rho_b = (real *)calloc(n, sizeof(real));
+    s->ux = (real *)calloc(n, sizeof(real));
+    s->uy = (real *)calloc(n, sizeof(real));
+    s->psi = (real *)calloc(n, sizeof(real));
+    s->Qx = (real *)calloc(2 * n, sizeof(real));
+    s->Qy = (real *)calloc(2 * n, sizeof(real));
     return s;
 }
 
@@ -424,26 +432,26 @@ void orc_destroy(orc_sim *s) {
 
 long orc_time(const orc_sim *s) { return s->t; }
 
-void orc_set_pops(orc_sim *s, const double *pop) {
-    memcpy(s->N, pop, 18 * (size_t)s->p.nx * s->p.ny * sizeof(double));
+void orc_set_pops(orc_sim *s, const real *pop) {
+    memcpy(s->N, pop, 18 * (size_t)s->p.nx * s->p.ny * sizeof(real));
 }
 
-void orc_get_pops(const orc_sim *s, double *pop) {
-    memcpy(pop, s->N, 18 * (size_t)s->p.nx * s->p.ny * sizeof(double));
+void orc_get_pops(const orc_sim *s, real *pop) {
+    memcpy(pop, s->N, 18 * (size_t)s->p.nx * s->p.ny * sizeof(real));
 }
 
-static void gather_node(const orc_sim *s, const double *pop, int x, int y, double *Nk) {
+static void gather_node(const orc_sim *s, const real *pop, int x, int y, real *Nk) {
     for (int k = 0; k < 2; k++)
         for (int i = 0; i < 9; i++) Nk[9 * k + i] = pop[pidx(s, k, i, x, y)];
 }
 
-static void scatter_node(orc_sim *s, double *pop, int x, int y, const double *Nk) {
+static void scatter_node(orc_sim *s, real *pop, int x, int y, const real *Nk) {
     for (int k = 0; k < 2; k++)
         for (int i = 0; i < 9; i++) pop[pidx(s, k, i, x, y)] = Nk[9 * k + i];
 }
 
 /* Red fraction injected at inlet row y at time t. */
-static double inlet_red_fraction(const orc_params *p, int y, long t) {
+static real inlet_red_fraction(const orc_params *p, int y, long t) {
     if (p->inlet_mode == ORC_INLET_LAYERED) return y < p->inlet_layer ? 1.0 : 0.0;
     long period = (long)p->inlet_period_r + p->inlet_period_b;
     if (period <= 0) return 1.0;
@@ -453,7 +461,7 @@ static double inlet_red_fraction(const orc_params *p, int y, long t) {
 static void apply_inout(orc_sim *s) {
     if (s->p.bc_x != ORC_INOUT) return;
     for (int y = 0; y < s->p.ny; y++) {
-        double Nk[18];
+        real Nk[18];
         gather_node(s, s->N, 0, y, Nk);
         orc_zouhe_inlet(&s->p, inlet_red_fraction(&s->p, y, s->t), Nk, Nk + 9);
         scatter_node(s, s->N, 0, y, Nk);
@@ -463,13 +471,13 @@ static void apply_inout(orc_sim *s) {
     }
 }
 
-void orc_init_fields(orc_sim *s, const double *rho_r, const double *rho_b, const double *ux,
-                     const double *uy) {
+void orc_init_fields(orc_sim *s, const real *rho_r, const real *rho_b, const real *ux,
+                     const real *uy) {
     int nx = s->p.nx, ny = s->p.ny;
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t n = (size_t)y * nx + x;
-            double er[9], eb[9];
+            real er[9], eb[9];
             orc_equilibrium(&s->p, 0, rho_r[n], ux[n], uy[n], er);
             orc_equilibrium(&s->p, 1, rho_b[n], ux[n], uy[n], eb);
             for (int i = 0; i < 9; i++) {
@@ -501,7 +509,7 @@ static int in_domain(const orc_params *p, int X, int Y, int *xw, int *yw) {
  * (a solid node) it is the W-weighted mean of the in-domain neighbours
  * (Sec. 2.4 extrapolation); behind an open inlet / outlet column it is the
  * value of the boundary node on the same row (zero normal gradient). */
-static double psi_at(const orc_sim *s, int X, int Y) {
+static real psi_at(const orc_sim *s, int X, int Y) {
     int xw, yw;
     if (in_domain(&s->p, X, Y, &xw, &yw)) return s->psi[(size_t)yw * s->p.nx + xw];
     int out_y = (Y < 0 || Y >= s->p.ny);
@@ -509,7 +517,7 @@ static double psi_at(const orc_sim *s, int X, int Y) {
         int xc = X < 0 ? 0 : s->p.nx - 1;
         return s->psi[(size_t)Y * s->p.nx + xc];
     }
-    double num = 0.0, den = 0.0;
+    real num = 0.0, den = 0.0;
     for (int i = 1; i < 9; i++)
         if (in_domain(&s->p, X + CX[i], Y + CY[i], &xw, &yw)) {
             num += W(i) * s->psi[(size_t)yw * s->p.nx + xw];
@@ -521,8 +529,8 @@ static double psi_at(const orc_sim *s, int X, int Y) {
 /* Q^k (component comp: 0 x, 1 y) at any lattice position next to the domain:
  * zero behind a no-slip wall (u = 0 there), the boundary node's value behind
  * an open inlet / outlet column (zero normal gradient). */
-static double Q_at(const orc_sim *s, int k, int comp, int X, int Y) {
-    const double *Q = comp == 0 ? s->Qx : s->Qy;
+static real Q_at(const orc_sim *s, int k, int comp, int X, int Y) {
+    const real *Q = comp == 0 ? s->Qx : s->Qy;
     size_t n = (size_t)s->p.nx * s->p.ny;
     int xw, yw;
     if (in_domain(&s->p, X, Y, &xw, &yw)) return Q[k * n + (size_t)yw * s->p.nx + xw];
@@ -539,11 +547,12 @@ static void moments_pass(orc_sim *s) {
     const orc_params *p = &s->p;
     int nx = p->nx, ny = p->ny;
     size_t n = (size_t)nx * ny;
-    double ar = alpha_of(p, 0), ab = alpha_of(p, 1);
+    real ar = alpha_of(p, 0), ab = alpha_of(p, 1);
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t c = (size_t)y * nx + x;
-            double Nk[18];
+            real Nk[18];
             gather_node(s, s->N, x, y, Nk);
             node_moments(p, Nk, &s->rho_r[c], &s->rho_b[c], &s->ux[c], &s->uy[c]);
             s->psi[c] = colour_field(p, s->rho_r[c], s->rho_b[c]);
@@ -557,13 +566,13 @@ static void moments_pass(orc_sim *s) {
 
 /* Colour gradient F (Eq. (eq:colorGradient)) and the S2I4 derivatives
  * d_x Q^k_x, d_y Q^k_y of one node, from the fields of moments_pass. */
-static void gradient_node(const orc_sim *s, int x, int y, double *Fx, double *Fy,
-                          double dQ[2][2]) {
+static void gradient_node(const orc_sim *s, int x, int y, real *Fx, real *Fy,
+                          real dQ[2][2]) {
     *Fx = 0.0;
     *Fy = 0.0;
     dQ[0][0] = dQ[0][1] = dQ[1][0] = dQ[1][1] = 0.0;
     for (int i = 1; i < 9; i++) {
-        double ps = psi_at(s, x + CX[i], y + CY[i]);
+        real ps = psi_at(s, x + CX[i], y + CY[i]);
         *Fx += xi(i) * CX[i] * ps;
         *Fy += xi(i) * CY[i] * ps;
         for (int k = 0; k < 2; k++) {
@@ -579,22 +588,22 @@ static void gradient_node(const orc_sim *s, int x, int y, double *Fx, double *Fy
  * the angle theta with the wall normal n^s (pointing into the fluid) is closer to
  * it, n^s itself on a tie; |F| is kept.  Applied to walls in y (a node next to
  * both walls of a one-row channel takes the bottom one). */
-static void contact_angle_adjust(const orc_params *p, int x, int y, double *Fx, double *Fy) {
+static void contact_angle_adjust(const orc_params *p, int x, int y, real *Fx, real *Fy) {
     (void)x;
-    if (p->contact_angle <= 0.0 || p->bc_y != ORC_WALL) return;
-    double nsx = 0.0, nsy;
+    if ((real)p->contact_angle <= 0.0 || p->bc_y != ORC_WALL) return;
+    real nsx = 0.0, nsy;
     if (y == 0) nsy = 1.0;
     else if (y == p->ny - 1) nsy = -1.0;
     else return;
-    double F = sqrt(*Fx * *Fx + *Fy * *Fy);
+    real F = sqrt(*Fx * *Fx + *Fy * *Fy);
     if (F == 0.0) return;
-    double ct = cos(p->contact_angle), st = sin(p->contact_angle);
-    double n1x = nsx * ct - nsy * st, n1y = nsy * ct + nsx * st;
-    double n2x = nsx * ct + nsy * st, n2y = nsy * ct - nsx * st;
-    double ux = *Fx / F, uy = *Fy / F;
-    double d1 = sqrt((ux - n1x) * (ux - n1x) + (uy - n1y) * (uy - n1y));
-    double d2 = sqrt((ux - n2x) * (ux - n2x) + (uy - n2y) * (uy - n2y));
-    double nx_, ny_;
+    real ct = cos((real)p->contact_angle), st = sin((real)p->contact_angle);
+    real n1x = nsx * ct - nsy * st, n1y = nsy * ct + nsx * st;
+    real n2x = nsx * ct + nsy * st, n2y = nsy * ct - nsx * st;
+    real ux = *Fx / F, uy = *Fy / F;
+    real d1 = sqrt((ux - n1x) * (ux - n1x) + (uy - n1y) * (uy - n1y));
+    real d2 = sqrt((ux - n2x) * (ux - n2x) + (uy - n2y) * (uy - n2y));
+    real nx_, ny_;
     if (d1 < d2) { nx_ = n1x; ny_ = n1y; }
     else if (d1 > d2) { nx_ = n2x; ny_ = n2y; }
     else { nx_ = nsx; ny_ = nsy; }
@@ -602,14 +611,14 @@ static void contact_angle_adjust(const orc_params *p, int x, int y, double *Fx, 
     *Fy = F * ny_;
 }
 
-void orc_gradient_fields(orc_sim *s, double *Fx, double *Fy, double *dQ) {
+void orc_gradient_fields(orc_sim *s, real *Fx, real *Fy, real *dQ) {
     moments_pass(s);
     int nx = s->p.nx, ny = s->p.ny;
     size_t n = (size_t)nx * ny;
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t c = (size_t)y * nx + x;
-            double fx, fy, d[2][2];
+            real fx, fy, d[2][2];
             gradient_node(s, x, y, &fx, &fy, d);
             contact_angle_adjust(&s->p, x, y, &fx, &fy);
             if (Fx) Fx[c] = fx;
@@ -631,13 +640,14 @@ static void step_once(orc_sim *s) {
     moments_pass(s);
 
     /* 2. colour gradient, collision, perturbation, recolouring per node */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t c = (size_t)y * nx + x;
-            double Fx, Fy, dQ[2][2];
+            real Fx, Fy, dQ[2][2];
             gradient_node(s, x, y, &Fx, &Fy, dQ);
             contact_angle_adjust(p, x, y, &Fx, &Fy);
-            double Nk[18], Nstar[18], Nsum[9], Nr[9], Nb[9];
+            real Nk[18], Nstar[18], Nsum[9], Nr[9], Nb[9];
             gather_node(s, s->N, x, y, Nk);
             orc_collide_node(p, Nk, Fx, Fy, dQ[0][0], dQ[0][1], dQ[1][0], dQ[1][1], Nstar);
             for (int i = 0; i < 9; i++) Nsum[i] = Nstar[i] + Nstar[9 + i];
@@ -649,13 +659,14 @@ static void step_once(orc_sim *s) {
         }
 
     /* 3. streaming, Eq. (eq:subop4), with periodic / bounce-back links */
+#pragma omp parallel for collapse(3) schedule(static)
     for (int k = 0; k < 2; k++)
         for (int i = 0; i < 9; i++)
             for (int y = 0; y < ny; y++)
                 for (int x = 0; x < nx; x++) {
                     int X = x - CX[i], Y = y - CY[i];
                     int xw, yw;
-                    double v;
+                    real v;
                     int out_y = (Y < 0 || Y >= ny), out_x = (X < 0 || X >= nx);
                     int wall_y = out_y && p->bc_y == ORC_WALL, wall_x = out_x && p->bc_x == ORC_WALL;
                     if (in_domain(p, X, Y, &xw, &yw))
@@ -682,14 +693,14 @@ void orc_step(orc_sim *s, long n) {
     for (long j = 0; j < n; j++) step_once(s);
 }
 
-void orc_fields(const orc_sim *s, double *rho_r, double *rho_b, double *ux, double *uy,
-                double *p, double *psi) {
+void orc_fields(const orc_sim *s, real *rho_r, real *rho_b, real *ux, real *uy,
+                real *p, real *psi) {
     int nx = s->p.nx, ny = s->p.ny;
-    double cr = cs2_of(&s->p, 0), cb = cs2_of(&s->p, 1);
+    real cr = cs2_of(&s->p, 0), cb = cs2_of(&s->p, 1);
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             size_t c = (size_t)y * nx + x;
-            double Nk[18], rr, rb, vx, vy;
+            real Nk[18], rr, rb, vx, vy;
             gather_node(s, s->N, x, y, Nk);
             node_moments(&s->p, Nk, &rr, &rb, &vx, &vy);
             if (rho_r) rho_r[c] = rr;

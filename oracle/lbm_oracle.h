@@ -24,6 +24,15 @@
 extern "C" {
 #endif
 
+/* Arithmetic type of the oracle: FP64 (the default).  The tests also compile
+ * the same source with ORC_REAL=float and single-precision constants, to
+ * measure what FP32 rounding alone does to a case (the method's FP32 floor);
+ * the parameters below stay double either way. */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL orc_real;
+
 enum { ORC_BGK = 0, ORC_MRT = 1 };
 enum { ORC_EQ_STD = 0, ORC_EQ_HERMITE = 1 };
 enum { ORC_PERIODIC = 0, ORC_WALL = 1, ORC_INOUT = 2 };
@@ -64,12 +73,12 @@ void orc_destroy(orc_sim *s);
 long orc_time(const orc_sim *s);
 
 /* State: pre-collision populations N^k_i(x, t). */
-void orc_set_pops(orc_sim *s, const double *pop);
-void orc_get_pops(const orc_sim *s, double *pop);
+void orc_set_pops(orc_sim *s, const orc_real *pop);
+void orc_get_pops(const orc_sim *s, orc_real *pop);
 
 /* Equilibrium initial state from macroscopic fields (nx*ny each, x fastest). */
-void orc_init_fields(orc_sim *s, const double *rho_r, const double *rho_b,
-                     const double *ux, const double *uy);
+void orc_init_fields(orc_sim *s, const orc_real *rho_r, const orc_real *rho_b,
+                     const orc_real *ux, const orc_real *uy);
 
 /* n full time steps. */
 void orc_step(orc_sim *s, long n);
@@ -77,29 +86,29 @@ void orc_step(orc_sim *s, long n);
 /* Macroscopic fields of the current state: rho_r, rho_b, u (Guo half-force
  * included), p = sum_k rho_k (c_s^k)^2 (Eq. (eq:pressureRelation)), psi. Any
  * output pointer may be NULL. */
-void orc_fields(const orc_sim *s, double *rho_r, double *rho_b, double *ux,
-                double *uy, double *p, double *psi);
+void orc_fields(const orc_sim *s, orc_real *rho_r, orc_real *rho_b, orc_real *ux,
+                orc_real *uy, orc_real *p, orc_real *psi);
 
 /* Colour gradient F and S2I4 derivatives of Q^k for every node of the current
  * state; dQ layout [4][ny][nx] = d_xQ^r_x, d_yQ^r_y, d_xQ^b_x, d_yQ^b_y. */
-void orc_gradient_fields(orc_sim *s, double *Fx, double *Fy, double *dQ);
+void orc_gradient_fields(orc_sim *s, orc_real *Fx, orc_real *Fy, orc_real *dQ);
 
 /* ---- single operators, exposed so tests can pin them one by one ---- */
-void orc_derived(const orc_params *p, double *alpha_r, double *omega_r, double *omega_b,
-                 double *chi, double *eta, double *kappa, double *lam, double *nu);
-void orc_equilibrium(const orc_params *p, int k, double rho_k, double ux, double uy,
-                     double *neq /* 9 */);
-double orc_omega_eff(const orc_params *p, double psi);
-void orc_perturbation(const orc_params *p, double A, double Fx, double Fy,
-                      double *dN /* 9, increment for one colour */);
-void orc_recolour(const orc_params *p, double rho_r, double rho_b, double Fx, double Fy,
-                  const double *N /* 9 colour-blind */, double *Nr, double *Nb);
-void orc_mrt_matrices(double *M /* 81 */, double *Minv /* 81 */);
-void orc_collide_node(const orc_params *p, const double *Nk /* 2*9 */, double Fx, double Fy,
-                      double divQr_x, double divQr_y, double divQb_x, double divQb_y,
-                      double *Nstar /* 2*9, after collision + perturbation */);
-void orc_zouhe_inlet(const orc_params *p, double f_r, double *Nr /* 9 */, double *Nb /* 9 */);
-void orc_zouhe_outlet(const orc_params *p, double *Nr /* 9 */, double *Nb /* 9 */);
+void orc_derived(const orc_params *p, orc_real *alpha_r, orc_real *omega_r, orc_real *omega_b,
+                 orc_real *chi, orc_real *eta, orc_real *kappa, orc_real *lam, orc_real *nu);
+void orc_equilibrium(const orc_params *p, int k, orc_real rho_k, orc_real ux, orc_real uy,
+                     orc_real *neq /* 9 */);
+orc_real orc_omega_eff(const orc_params *p, orc_real psi);
+void orc_perturbation(const orc_params *p, orc_real A, orc_real Fx, orc_real Fy,
+                      orc_real *dN /* 9, increment for one colour */);
+void orc_recolour(const orc_params *p, orc_real rho_r, orc_real rho_b, orc_real Fx, orc_real Fy,
+                  const orc_real *N /* 9 colour-blind */, orc_real *Nr, orc_real *Nb);
+void orc_mrt_matrices(orc_real *M /* 81 */, orc_real *Minv /* 81 */);
+void orc_collide_node(const orc_params *p, const orc_real *Nk /* 2*9 */, orc_real Fx, orc_real Fy,
+                      orc_real divQr_x, orc_real divQr_y, orc_real divQb_x, orc_real divQb_y,
+                      orc_real *Nstar /* 2*9, after collision + perturbation */);
+void orc_zouhe_inlet(const orc_params *p, orc_real f_r, orc_real *Nr /* 9 */, orc_real *Nb /* 9 */);
+void orc_zouhe_outlet(const orc_params *p, orc_real *Nr /* 9 */, orc_real *Nb /* 9 */);
 
 #ifdef __cplusplus
 }

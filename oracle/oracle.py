@@ -89,15 +89,18 @@ def build(force: bool = False) -> str:
              or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
     if force or stale:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
 
-def bind(path: str) -> ctypes.CDLL:
-    """Load an oracle shared library and declare its C signatures."""
+def bind(path: str, real=ctypes.c_double) -> ctypes.CDLL:
+    """Load an oracle shared library and declare its C signatures.  `real` is the
+    library's arithmetic type (ctypes.c_double, or ctypes.c_float for a build
+    with ORC_REAL=float); arrays passed to it use the matching numpy dtype."""
     L = ctypes.CDLL(path)
-    dp = ctypes.POINTER(ctypes.c_double)
+    L.real_dtype = np.float64 if real is ctypes.c_double else np.float32
+    dp = ctypes.POINTER(real)
     pp = ctypes.POINTER(_Params)
     L.orc_create.restype = ctypes.c_void_p
     L.orc_create.argtypes = [pp]
@@ -111,31 +114,38 @@ def bind(path: str) -> ctypes.CDLL:
     L.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp, dp]
     L.orc_gradient_fields.argtypes = [ctypes.c_void_p, dp, dp, dp]
     L.orc_derived.argtypes = [pp] + [dp] * 8
-    L.orc_equilibrium.argtypes = [pp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                  ctypes.c_double, dp]
-    L.orc_omega_eff.restype = ctypes.c_double
-    L.orc_omega_eff.argtypes = [pp, ctypes.c_double]
-    L.orc_perturbation.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
-    L.orc_recolour.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                               ctypes.c_double, dp, dp, dp]
+    L.orc_equilibrium.argtypes = [pp, ctypes.c_int, real, real, real, dp]
+    L.orc_omega_eff.restype = real
+    L.orc_omega_eff.argtypes = [pp, real]
+    L.orc_perturbation.argtypes = [pp, real, real, real, dp]
+    L.orc_recolour.argtypes = [pp, real, real, real, real, dp, dp, dp]
     L.orc_mrt_matrices.argtypes = [dp, dp]
-    L.orc_collide_node.argtypes = [pp, dp, ctypes.c_double, ctypes.c_double] + \
-        [ctypes.c_double] * 4 + [dp]
-    L.orc_zouhe_inlet.argtypes = [pp, ctypes.c_double, dp, dp]
+    L.orc_collide_node.argtypes = [pp, dp, real, real] + [real] * 4 + [dp]
+    L.orc_zouhe_inlet.argtypes = [pp, real, dp, dp]
     L.orc_zouhe_outlet.argtypes = [pp, dp, dp]
     return L
 
 
-def compile_variant(source_text: str, out_dir: str) -> str:
-    """Compile a modified copy of the oracle source (the tests plant mistakes in
-    it to show that the pins catch them) into out_dir; returns the library path."""
+def compile_variant(source_text: str, out_dir: str, flags=()) -> str:
+    """Compile a copy of the oracle source, possibly modified (the tests plant
+    mistakes in it to show that the pins catch them), with extra gcc flags into
+    out_dir; returns the library path."""
     src = os.path.join(out_dir, "lbm_oracle_variant.c")
     with open(src, "w") as f:
         f.write(source_text)
     so = os.path.join(out_dir, "liblbm_oracle_variant.so")
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-I", _HERE, "-o", so, src,
-                           "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fopenmp", "-shared", "-fPIC", *flags, "-I", _HERE, "-o",
+                           so, src, "-lm"])
     return so
+
+
+def fp32_library(out_dir: str) -> ctypes.CDLL:
+    """The oracle source built with an FP32 arithmetic type and single-precision
+    constants (parameters are still given in double): what FP32 rounding alone
+    does to a case, with no other difference from the FP64 oracle."""
+    src = open(_SRC).read()
+    return bind(compile_variant(src, out_dir, ("-DORC_REAL=float", "-fsingle-precision-constant")),
+                real=ctypes.c_float)
 
 
 _lib = None
@@ -149,8 +159,9 @@ def lib():
 
 
 def _ptr(a: np.ndarray):
-    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
-    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert a.dtype in (np.float64, np.float32) and a.flags["C_CONTIGUOUS"]
+    ct = ctypes.c_double if a.dtype == np.float64 else ctypes.c_float
+    return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
 def _f64(a) -> np.ndarray:
@@ -161,10 +172,12 @@ class Oracle:
     """One FP64 simulation.  State = pre-collision populations N^k_i(x, t),
     array shape (2, 9, ny, nx), k = 0 red (heavy), 1 blue (light)."""
 
-    def __init__(self, params: OracleParams):
+    def __init__(self, params: OracleParams, library=None):
+        """library: a bound oracle library (default: the FP64 oracle)."""
         self.params = params
         self._cp = params.to_c()
-        self._L = lib()
+        self._L = library if library is not None else lib()
+        self._dt = self._L.real_dtype
         self._h = self._L.orc_create(ctypes.byref(self._cp))
 
     def __del__(self):
@@ -182,26 +195,26 @@ class Oracle:
         return self._L.orc_time(self._h)
 
     def init_fields(self, rho_r, rho_b, ux, uy):
-        a = [_f64(v).reshape(self.shape) for v in (rho_r, rho_b, ux, uy)]
+        a = [np.ascontiguousarray(v, dtype=self._dt).reshape(self.shape) for v in (rho_r, rho_b, ux, uy)]
         self._L.orc_init_fields(self._h, *[_ptr(v) for v in a])
 
     def set_pops(self, pops):
-        a = _f64(pops).reshape((2, 9) + self.shape)
+        a = np.ascontiguousarray(pops, dtype=self._dt).reshape((2, 9) + self.shape)
         self._L.orc_set_pops(self._h, _ptr(a))
 
     def get_pops(self) -> np.ndarray:
-        out = np.empty((2, 9) + self.shape)
+        out = np.empty((2, 9) + self.shape, dtype=self._dt)
         self._L.orc_get_pops(self._h, _ptr(out))
-        return out
+        return out.astype(np.float64)
 
     def step(self, n: int = 1):
         self._L.orc_step(self._h, int(n))
 
     def fields(self) -> dict:
         names = ("rho_r", "rho_b", "ux", "uy", "p", "psi")
-        out = {k: np.empty(self.shape) for k in names}
+        out = {k: np.empty(self.shape, dtype=self._dt) for k in names}
         self._L.orc_fields(self._h, *[_ptr(out[k]) for k in names])
-        return out
+        return {k: v.astype(np.float64) for k, v in out.items()}
 
 
 # ---- single operators (for pins) ----
@@ -272,6 +285,7 @@ def zouhe_outlet(params: OracleParams, Nr, Nb):
 def gradient_fields(o: Oracle):
     """Colour gradient F and the S2I4 derivatives of Q^k for every node."""
     ny, nx = o.shape
-    Fx, Fy, dQ = np.empty(o.shape), np.empty(o.shape), np.empty((4, ny, nx))
+    Fx, Fy, dQ = (np.empty(o.shape, dtype=o._dt), np.empty(o.shape, dtype=o._dt),
+                  np.empty((4, ny, nx), dtype=o._dt))
     o._L.orc_gradient_fields(o._h, _ptr(Fx), _ptr(Fy), _ptr(dQ))
     return Fx, Fy, dQ

@@ -3,8 +3,10 @@
     python -m paper_1903_01168_gb300.build [--force] [--verbose]
 
 Produces ``paper_1903_01168_gb300/_native/liblbm_gb300.so`` from
-``paper_1903_01168_gb300/csrc/*.cu`` and ``include/lbm.h``.  Rebuilds only when a
-source is newer than the library.
+``paper_1903_01168_gb300/csrc/*.cu`` and ``include/lbm.h``.  Each translation unit
+is compiled to an object in parallel (the step kernels of each storage type sit in
+their own units), then the objects are linked.  Rebuilds only when a source is
+newer than the library.
 """
 from __future__ import annotations
 
@@ -12,6 +14,7 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -44,24 +47,43 @@ def stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps())
 
 
-def command(out: str, extra: list[str] | None = None) -> list[str]:
-    return [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-            "-I", INCLUDE, "-I", CSRC, *(extra or []), "-o", out, *sources()]
+def compile_command(src: str, obj: str, extra: list[str] | None = None) -> list[str]:
+    return [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+            *(extra or []), "-c", "-o", obj, src]
+
+
+def link_command(objs: list[str], out: str) -> list[str]:
+    return [nvcc(), *ARCH, "-shared", "-o", out, *objs]
+
+
+def _run(cmd: list[str]) -> subprocess.CompletedProcess:
+    return subprocess.run(cmd, capture_output=True, text=True)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the library if needed and return its path."""
     if not force and not stale():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    obj_dir = os.path.join(OUT_DIR, "obj")
+    os.makedirs(obj_dir, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose else []
-    cmd = command(tmp, extra)
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    srcs = sources()
+    tag = f".{os.getpid()}"
+    objs = [os.path.join(obj_dir, os.path.basename(p)[:-3] + tag + ".o") for p in srcs]
+    cmds = [compile_command(p, o, extra) for p, o in zip(srcs, objs)]
+    with ThreadPoolExecutor(max_workers=min(len(cmds), max(1, os.cpu_count() or 1))) as ex:
+        results = list(ex.map(_run, cmds))
+    for cmd, res in zip(cmds, results):
+        if res.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
+        if verbose:
+            sys.stderr.write(res.stdout + res.stderr)
+    tmp = LIB + tag + ".tmp"
+    res = _run(link_command(objs, tmp))
+    for o in objs:
+        os.remove(o)
     if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
-    if verbose:
-        sys.stderr.write(res.stdout + res.stderr)
+        raise RuntimeError("nvcc link failed:\n" + res.stdout + res.stderr)
     os.replace(tmp, LIB)
     return LIB
 

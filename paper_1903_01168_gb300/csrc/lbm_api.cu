@@ -24,9 +24,6 @@ using namespace lbm;
 
 namespace {
 
-constexpr int FUSED_W = 128;     // columns per strip = threads per block
-constexpr int FUSED_NSLOT = 4;   // shared-memory row slots per block
-
 thread_local char g_create_err[256] = "";
 
 void set_err(char *buf, const char *fmt, ...) {
@@ -51,16 +48,6 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     });
     return fn;
-}
-
-template <typename T, int CV>
-const void *fused_kernel_ptr() {
-    return reinterpret_cast<const void *>(&k_step_fused<T, CV, FUSED_W, FUSED_NSLOT>);
-}
-
-template <typename T, int CV>
-int fused_smem() {
-    return FusedCfg<T, CV, FUSED_W, FUSED_NSLOT>::SMEM;
 }
 
 int variant_of(const lbm_params *p) {
@@ -251,7 +238,8 @@ void fill_desc(SimDesc &h, int nx, int ny, const lbm_params *p) {
     f.gx = (float)p->gx;
     f.gy = (float)p->gy;
     f.mrt_lambda = (float)p->mrt_lambda;
-    f.c7 = (float)p->c7_sign;
+    f.c7x = (float)p->c7_factor;
+    f.c7y = (float)(p->c7_factor * p->c7_sign);
     const double cs2_r = 3.0 * (1.0 - alpha_r) / 5.0, cs2_b = 3.0 * (1.0 - alpha_b) / 5.0;
     f.cs2_r = (float)cs2_r;
     f.cs2_b = (float)cs2_b;
@@ -463,40 +451,12 @@ Plan make_plan(const std::vector<StripRef> &strips, int kind, int rows_per_item,
     return split_plan(strips, max_blocks, row_overhead);
 }
 
-template <typename T, int CV>
-cudaError_t launch_fused_t(const SimDesc *descs, const WorkItem *items, const int *item_off, int n_blocks, int off,
-                           int *err, cudaStream_t st) {
-    static bool attr_done[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel_ptr<T, CV>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             fused_smem<T, CV>());
-        if (e != cudaSuccess) return e;
-        attr_done[dev] = true;
-    }
-    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_blocks, FUSED_W, fused_smem<T, CV>(), st>>>(descs, items, item_off,
-                                                                                       n_blocks, off, err);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_fused_v(int variant, const SimDesc *descs, const WorkItem *items, const int *item_off,
-                           int n_blocks, int off, int *err, cudaStream_t st) {
-    switch (variant) {
-    case 0: return launch_fused_t<T, 0>(descs, items, item_off, n_blocks, off, err, st);
-    case CV_MRT: return launch_fused_t<T, CV_MRT>(descs, items, item_off, n_blocks, off, err, st);
-    case CV_HERMITE: return launch_fused_t<T, CV_HERMITE>(descs, items, item_off, n_blocks, off, err, st);
-    default: return launch_fused_t<T, CV_MRT | CV_HERMITE>(descs, items, item_off, n_blocks, off, err, st);
-    }
-}
-
 cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, const WorkItem *items,
                              const int *item_off, int n_blocks, int off, int *err, cudaStream_t st) {
     switch (storage) {
-    case ST_F32: return launch_fused_v<float>(variant, descs, items, item_off, n_blocks, off, err, st);
-    case ST_F16DEV: return launch_fused_v<__half>(variant, descs, items, item_off, n_blocks, off, err, st);
-    default: return launch_fused_v<__nv_bfloat16>(variant, descs, items, item_off, n_blocks, off, err, st);
+    case ST_F32: return fused_launch<float>(variant, descs, items, item_off, n_blocks, off, err, st);
+    case ST_F16DEV: return fused_launch<__half>(variant, descs, items, item_off, n_blocks, off, err, st);
+    default: return fused_launch<__nv_bfloat16>(variant, descs, items, item_off, n_blocks, off, err, st);
     }
 }
 
@@ -509,20 +469,12 @@ int resident_blocks(int storage, int variant) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void *k = nullptr;
-    int smem = 0;
-    switch (storage * 4 + variant) {
-#define LBM_RES_CASE(ST, T, CV)                 \
-    case ST * 4 + CV:                            \
-        k = fused_kernel_ptr<T, CV>();           \
-        smem = fused_smem<T, CV>();              \
-        break;
-        LBM_RES_CASE(0, float, 0) LBM_RES_CASE(0, float, 1) LBM_RES_CASE(0, float, 2) LBM_RES_CASE(0, float, 3)
-        LBM_RES_CASE(1, __half, 0) LBM_RES_CASE(1, __half, 1) LBM_RES_CASE(1, __half, 2) LBM_RES_CASE(1, __half, 3)
-        LBM_RES_CASE(2, __nv_bfloat16, 0) LBM_RES_CASE(2, __nv_bfloat16, 1) LBM_RES_CASE(2, __nv_bfloat16, 2)
-        LBM_RES_CASE(2, __nv_bfloat16, 3)
-#undef LBM_RES_CASE
-    }
+    const void *k = storage == ST_F32 ? fused_kernel<float>(variant)
+                    : storage == ST_F16DEV ? fused_kernel<__half>(variant)
+                                           : fused_kernel<__nv_bfloat16>(variant);
+    const int smem = storage == ST_F32 ? fused_smem<float>(variant)
+                     : storage == ST_F16DEV ? fused_smem<__half>(variant)
+                                            : fused_smem<__nv_bfloat16>(variant);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, FUSED_W, smem) != cudaSuccess || per < 1) per = 1;
     if (sms < 1) sms = 1;
@@ -535,30 +487,12 @@ int grid_for(long long n, int threads) {
     return (int)std::max<long long>(1, std::min<long long>(g, 152LL * 16));
 }
 
-template <typename T, int CV>
-cudaError_t launch_twopass_t(lbm_sim *s, int off) {
-    const long long n = (long long)s->nx * s->ny;
-    const int g = grid_for(n, 256);
-    k_tp_moments<T, CV><<<g, 256, 0, s->stream>>>(s->d_desc, off, s->d_aux);
-    k_tp_collide<T, CV><<<g, 256, 0, s->stream>>>(s->d_desc, off, s->d_aux);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_twopass_v(lbm_sim *s, int off) {
-    switch (s->h.variant) {
-    case 0: return launch_twopass_t<T, 0>(s, off);
-    case CV_MRT: return launch_twopass_t<T, CV_MRT>(s, off);
-    case CV_HERMITE: return launch_twopass_t<T, CV_HERMITE>(s, off);
-    default: return launch_twopass_t<T, CV_MRT | CV_HERMITE>(s, off);
-    }
-}
-
 cudaError_t launch_twopass(lbm_sim *s, int off) {
+    const long long n = (long long)s->nx * s->ny;
     switch (s->p.storage) {
-    case ST_F32: return launch_twopass_v<float>(s, off);
-    case ST_F16DEV: return launch_twopass_v<__half>(s, off);
-    default: return launch_twopass_v<__nv_bfloat16>(s, off);
+    case ST_F32: return twopass_launch<float>(s->h.variant, s->d_desc, off, s->d_aux, n, s->stream);
+    case ST_F16DEV: return twopass_launch<__half>(s->h.variant, s->d_desc, off, s->d_aux, n, s->stream);
+    default: return twopass_launch<__nv_bfloat16>(s->h.variant, s->d_desc, off, s->d_aux, n, s->stream);
     }
 }
 
@@ -614,6 +548,90 @@ void launch_diag(lbm_sim *s, int pass, double cx, double cy, double rin, double 
     case ST_F16DEV: launch_diag_s<__half>(s, pass, cx, cy, rin, rout); break;
     default: launch_diag_s<__nv_bfloat16>(s, pass, cx, cy, rin, rout); break;
     }
+}
+
+template <typename T>
+void launch_slug_profile_s(lbm_sim *s, double *out) {
+    const int g = std::max(1, (s->nx + 127) / 128);
+    if (s->h.variant & CV_HERMITE) k_slug_profile<T, true><<<g, 128, 0, s->stream>>>(s->d_desc, s->t, out);
+    else k_slug_profile<T, false><<<g, 128, 0, s->stream>>>(s->d_desc, s->t, out);
+}
+
+void launch_slug_profile(lbm_sim *s, double *out) {
+    switch (s->p.storage) {
+    case ST_F32: launch_slug_profile_s<float>(s, out); break;
+    case ST_F16DEV: launch_slug_profile_s<__half>(s, out); break;
+    default: launch_slug_profile_s<__nv_bfloat16>(s, out); break;
+    }
+}
+
+// Bubble / slug geometry of lbm_slug from the column profile g and the
+// centreline profile pc (both nx values).  Zeros of pc are located on the
+// linear interpolant between nodes x and x + 1.
+void slug_from_profile(const double *g, const double *pc, int nx, int ny, bool periodic, lbm_slug *o) {
+    struct Cross { double x; bool tail; };
+    std::vector<Cross> c;
+    const int last = periodic ? nx : nx - 1;
+    for (int x = 0; x < last; x++) {
+        const int x1 = x + 1 == nx ? 0 : x + 1;
+        const double a = pc[x], b = pc[x1];
+        if ((a >= 0.0) == (b >= 0.0)) continue;
+        double pos = x + a / (a - b);
+        if (pos >= nx) pos -= nx;
+        c.push_back({pos, a >= 0.0});
+    }
+    size_t start = 0;                  // the walk starts at the first tail
+    while (start < c.size() && !c[start].tail) start++;
+    if (start == c.size()) return;
+    const size_t m = c.size();
+    // bubbles: a tail followed by a nose (periodic lines wrap around)
+    std::vector<double> tails, noses;
+    for (size_t j = 0; j < m; j++) {
+        if (!periodic && start + j + 1 >= m) break;
+        const Cross &a = c[(start + j) % m], &b = c[(start + j + 1) % m];
+        if (a.tail && !b.tail) {
+            tails.push_back(a.x);
+            noses.push_back(b.x);
+        }
+    }
+    auto fwd = [&](double a, double b) {   // distance from a forward (+x) to b
+        const double d = b - a;
+        return periodic && d < 0.0 ? d + nx : d;
+    };
+    auto g_at = [&](double x) {            // g linear between columns
+        if (periodic) x = std::fmod(x, (double)nx);
+        x = std::min(std::max(x, 0.0), (double)(nx - 1) + (periodic ? 1.0 : 0.0));
+        const int i0 = std::min((int)std::floor(x), nx - 1);
+        const int i1 = i0 + 1 < nx ? i0 + 1 : (periodic ? 0 : nx - 1);
+        const double f = x - i0;
+        return (1.0 - f) * g[i0] + f * g[i1];
+    };
+    const size_t nb = tails.size();
+    double sb = 0.0, sf = 0.0, ss = 0.0;
+    int ns = 0;
+    for (size_t j = 0; j < nb; j++) {
+        const double len = fwd(tails[j], noses[j]);
+        sb += len;
+        sf += 0.5 * (ny - g_at(tails[j] + 0.5 * len));
+        if (j + 1 < nb) {
+            ss += fwd(noses[j], tails[j + 1]);
+            ns++;
+        } else if (periodic) {
+            ss += fwd(noses[j], tails[0]);   // around the line to the first bubble
+            ns++;
+        }
+        if (j < LBM_SLUG_MAX) {
+            o->x_tail[j] = tails[j];
+            o->x_nose[j] = noses[j];
+        }
+    }
+    o->n_bubbles = (int)nb;
+    o->n_slugs = ns;
+    if (nb > 0) {
+        o->bubble_len = sb / nb;
+        o->film = sf / nb;
+    }
+    if (ns > 0) o->slug_len = ss / ns;
 }
 
 // Wetting walls (free slip, contact angle) run on the two-pass kernels: the
@@ -806,7 +824,8 @@ lbm_status lbm_default_params(lbm_params *p) {
     p->sigma = 0.005;
     p->beta = 0.99;
     p->mrt_lambda = 0.8;
-    p->c7_sign = 1.0;
+    p->c7_sign = -1.0;
+    p->c7_factor = 1.0;
     return LBM_OK;
 }
 
@@ -1015,6 +1034,24 @@ lbm_status lbm_diagnostics(lbm_sim *s, lbm_diag *out) {
         return LBM_EUNSTABLE;
     }
     return LBM_OK;
+}
+
+lbm_status lbm_slug_geometry(lbm_sim *s, lbm_slug *out, double *gas) {
+    if (!s || !out) return LBM_EINVAL;
+    memset(out, 0, sizeof(*out));
+    const int nx = s->nx;
+    std::vector<double> h(2 * (size_t)nx);
+    double *d = nullptr;
+    CK(cudaMallocAsync(&d, 2 * (size_t)nx * sizeof(double), s->stream));
+    launch_slug_profile(s, d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h.data(), d, 2 * (size_t)nx * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaFreeAsync(d, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    out->t = s->t;
+    slug_from_profile(h.data(), h.data() + nx, nx, s->ny, s->p.bc_x == LBM_BC_PERIODIC, out);
+    if (gas) memcpy(gas, h.data(), (size_t)nx * sizeof(double));
+    return check_err_word(s, s->d_err);
 }
 
 size_t lbm_state_bytes(const lbm_sim *s) { return s ? s->pop_bytes + sizeof(long long) : 0; }

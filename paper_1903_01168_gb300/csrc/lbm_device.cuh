@@ -66,7 +66,8 @@ struct Phys {
     float dphi[3];             // phi_b - phi_r by |c|^2
     float omega_r, omega_b, chi, eta, kappa, lam, nu, delta;
     float a_coef;              // A = a_coef * omega_eff, a_coef = 9 sigma / 4
-    float beta, mrt_lambda, c7;
+    float beta, mrt_lambda;
+    float c7x, c7y;            // C^k_7 = (1 - omega_eff/2)(c7x d_xQ_x + c7y d_yQ_y)
     float herm_r, herm_b;      // 3 (c_s^k)^2 - 1
     float q_r, q_b;            // 1.8 alpha_k - 0.8
     float cs2_r, cs2_b;        // (c_s^k)^2
@@ -121,6 +122,9 @@ struct alignas(128) SimDesc {
     Phys ph;
     Wetting wet;
 };
+
+// Scratch field of the two-pass path: aux[5][ny][nx] = psi, rho_r, rho_b, q u_x, q u_y.
+constexpr int AUX_FIELDS = 5;
 
 // Collision variants (compile-time): bit 0 = MRT (else BGK), bit 1 = Hermite
 // equilibrium (with the U^k source when combined with MRT).
@@ -762,9 +766,11 @@ __device__ __forceinline__ void collide_node(const Phys &p, const Pulled &P, flo
             tm[a] = sa * m[a] - (1.0f - 0.5f * sa) * ms[a];
         }
         if (HERMITE) {
-            // + U = M^-1 C, C_1 = 3 (1 - s_1/2)(dQx + dQy), C_7 = 3 (1 - w/2)(dQx + c7 dQy)
+            // + U = M^-1 C, C_1 = 3 (1 - s_1/2)(dQx + dQy), C_7 = (1 - w/2)(dQx - dQy)
+            // (C_7's factor and sign from the Chapman-Enskog expansion: the p_xx
+            // moment carries d_xQ_x - d_yQ_y of the third-moment error)
             tm[1] -= 3.0f * (1.0f - 0.5f * s1) * (dQx + dQy);
-            tm[7] -= 3.0f * (1.0f - 0.5f * w) * (dQx + p.c7 * dQy);
+            tm[7] -= (1.0f - 0.5f * w) * (p.c7x * dQx + p.c7y * dQy);
         }
         // e -= M^-1 tm, M^-1 = (1/36) * integer matrix of the appendix (tm[0] = 0)
         const float k36 = 1.0f / 36.0f;

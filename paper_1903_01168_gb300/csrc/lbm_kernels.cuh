@@ -471,9 +471,6 @@ __global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__
 
 // --------------------------------------------------------- two-pass kernels
 
-// Scratch field of the two-pass path: aux[5][ny][nx] = psi, rho_r, rho_b, q u_x, q u_y.
-constexpr int AUX_FIELDS = 5;
-
 // Pass 1: colour field, colour densities and q u of every node.
 template <typename T, int CV>
 __global__ void k_tp_moments(const SimDesc *__restrict__ dp, int step_offset, float *__restrict__ aux) {
@@ -658,6 +655,33 @@ __global__ void k_fields(const SimDesc *__restrict__ dp, long long t, double *__
         out[2 * n + k] = m.ux;
         out[3 * n + k] = m.uy;
         out[4 * n + k] = (double)m.rr * p.cs2_r + (double)m.rb * p.cs2_b;
+    }
+}
+
+// Slug-train profile of the state at time t (the measurements of Sec. 5.1), in
+// FP64: per column x the light-phase thickness g(x) = sum_y (1 - psi)/2, and the
+// colour field psi_c(x) on the channel centreline (the middle row, or the mean
+// of the two middle rows when ny is even).  out[0, nx) = g, out[nx, 2 nx) = psi_c.
+// One thread per column; the threads of a warp read neighbouring columns.
+template <typename T, bool HERMITE>
+__global__ void k_slug_profile(const SimDesc *__restrict__ dp, long long t, double *__restrict__ out) {
+    const SimDesc &d = *dp;
+    const Phys p = d.ph;
+    const int nx = p.nx, ny = p.ny;
+    const GlobalLoader<T> L(d, (int)(t & 1));
+    const int ya = (ny - 1) / 2, yb = ny / 2;   // the same row when ny is odd
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+        double g = 0.0, pc = 0.0;
+        for (int y = 0; y < ny; y++) {
+            Pulled P;
+            pull_node<HERMITE>(p, L, x, y, t, false, 0.0f, 0.0f, P);
+            const double a = (double)P.rr * p.inv_gamma, b = (double)P.rb;
+            const double psi = (a - b) / (a + b);     // Eq. (eq:color_field)
+            g += 0.5 * (1.0 - psi);
+            if (y == ya || y == yb) pc += psi;
+        }
+        out[x] = g;
+        out[nx + x] = ya == yb ? pc : 0.5 * pc;
     }
 }
 

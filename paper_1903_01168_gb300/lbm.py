@@ -40,7 +40,7 @@ ABI_SYMBOLS = (
     "lbm_destroy", "lbm_batch_create", "lbm_batch_create_ex", "lbm_plan_preview", "lbm_batch_step",
     "lbm_batch_items",
     "lbm_batch_destroy",
-    "lbm_step_noalloc",
+    "lbm_step_noalloc", "lbm_slug_geometry",
 )
 
 
@@ -60,7 +60,7 @@ class lbm_params(ctypes.Structure):
         ("gx", ctypes.c_double), ("gy", ctypes.c_double),
         ("collision", ctypes.c_int), ("equilibrium", ctypes.c_int),
         ("mrt_lambda", ctypes.c_double), ("c7_sign", ctypes.c_double),
-        ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("storage", ctypes.c_int),
+        ("c7_factor", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int), ("storage", ctypes.c_int),
         ("u_in_r", ctypes.c_double), ("u_in_b", ctypes.c_double), ("p_out", ctypes.c_double),
         ("inlet_mode", ctypes.c_int), ("inlet_period_r", ctypes.c_int),
         ("inlet_period_b", ctypes.c_int), ("inlet_layer", ctypes.c_int),
@@ -82,6 +82,23 @@ class lbm_diag(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+LBM_SLUG_MAX = 16
+
+
+class lbm_slug(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_longlong), ("n_bubbles", ctypes.c_int), ("n_slugs", ctypes.c_int),
+        ("bubble_len", ctypes.c_double), ("slug_len", ctypes.c_double), ("film", ctypes.c_double),
+        ("x_tail", ctypes.c_double * LBM_SLUG_MAX), ("x_nose", ctypes.c_double * LBM_SLUG_MAX),
+    ]
+
+    def as_dict(self) -> dict:
+        n = min(self.n_bubbles, LBM_SLUG_MAX)
+        return {"t": self.t, "n_bubbles": self.n_bubbles, "n_slugs": self.n_slugs,
+                "bubble_len": self.bubble_len, "slug_len": self.slug_len, "film": self.film,
+                "x_tail": list(self.x_tail[:n]), "x_nose": list(self.x_nose[:n])}
 
 
 class LBMError(RuntimeError):
@@ -128,6 +145,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.lbm_read_fields.argtypes = [vp, dp, dp, dp, dp, dp]
     L.lbm_read_populations.argtypes = [vp, dp]
     L.lbm_diagnostics.argtypes = [vp, ctypes.POINTER(lbm_diag)]
+    L.lbm_slug_geometry.argtypes = [vp, ctypes.POINTER(lbm_slug), dp]
     L.lbm_state_bytes.argtypes = [vp]
     L.lbm_state_bytes.restype = st
     L.lbm_save_state.argtypes = [vp, vp, st]
@@ -240,6 +258,14 @@ def lbm_diagnostics(sim: int, allow_unstable: bool = False) -> dict:
     out = d.as_dict()
     out["status"] = st
     return out
+
+
+def lbm_slug_geometry(sim: int, nx: int) -> tuple[dict, np.ndarray]:
+    """Slug-train geometry (lbm_slug as a dict) and the column light thickness g(x)."""
+    o = lbm_slug()
+    gas = np.empty(nx)
+    _check(load().lbm_slug_geometry(sim, ctypes.byref(o), _dptr(gas)), sim)
+    return o.as_dict(), gas
 
 
 def lbm_state_bytes(sim: int) -> int:
@@ -413,6 +439,10 @@ class Simulation:
 
     def diagnostics(self, allow_unstable: bool = False) -> dict:
         return lbm_diagnostics(self.h, allow_unstable)
+
+    def slug_geometry(self) -> tuple[dict, np.ndarray]:
+        """(bubble / slug / film geometry, column light thickness g(x))."""
+        return lbm_slug_geometry(self.h, self.nx)
 
     def save_state(self) -> bytes:
         return lbm_save_state(self.h)

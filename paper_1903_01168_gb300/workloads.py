@@ -380,3 +380,54 @@ def laplace_pressure_jump(p: np.ndarray, psi: np.ndarray, cx: float, cy: float):
     area = ((1.0 - psi) / 2.0).sum()
     Reff = math.sqrt(area / math.pi)
     return p[r < Reff / 2].mean() - p[r > Reff + 8].mean(), Reff
+
+
+def slug_geometry(psi: np.ndarray, periodic: bool = True) -> dict:
+    """Geometry of a train of light bubbles moving along x (Sec. 5.1 measures),
+    from a colour field psi (ny, nx): the centreline profile psi_c (middle row, or
+    the mean of the two middle rows for even ny) and its zeros on the linear
+    interpolant between nodes (tail: psi_c from >= 0 to < 0 in +x; nose: from < 0
+    to >= 0); bubble length nose - tail; slug length from a nose to the next
+    tail; film thickness (ny - g(x_mid)) / 2 with g(x) = sum_y (1 - psi)/2 linear
+    between columns and x_mid the bubble's middle.  Returns a dict with
+    n_bubbles, n_slugs, bubble_len, slug_len, film (means), x_tail, x_nose, gas."""
+    ny, nx = psi.shape
+    ya, yb = (ny - 1) // 2, ny // 2
+    pc = 0.5 * (psi[ya] + psi[yb])
+    gas = ((1.0 - psi) / 2.0).sum(axis=0)
+    nxt = np.roll(pc, -1)
+    idx = np.nonzero((pc >= 0.0) != (nxt >= 0.0))[0]
+    if not periodic:
+        idx = idx[idx < nx - 1]
+    pos = (idx + pc[idx] / (pc[idx] - nxt[idx])) % nx
+    is_tail = pc[idx] >= 0.0
+    out = {"n_bubbles": 0, "n_slugs": 0, "bubble_len": 0.0, "slug_len": 0.0, "film": 0.0,
+           "x_tail": [], "x_nose": [], "gas": gas}
+    if not is_tail.any():
+        return out
+    first = int(np.argmax(is_tail))
+    order = np.arange(first, first + len(idx)) % len(idx) if periodic else np.arange(first, len(idx))
+    seq = [(pos[k], is_tail[k]) for k in order]
+    pairs = [(a[0], b[0]) for a, b in zip(seq, seq[1:] + (seq[:1] if periodic else [])) if a[1] and not b[1]]
+    if not pairs:
+        return out
+    tails = np.array([a for a, _ in pairs])
+    noses = np.array([b for _, b in pairs])
+    blen = noses - tails
+    if periodic:
+        blen = np.where(blen < 0, blen + nx, blen)
+    xm = tails + blen / 2.0
+    cols = np.arange(nx + 1)
+    gext = np.append(gas, gas[0] if periodic else gas[-1])
+    xm = xm % nx if periodic else np.clip(xm, 0, nx - 1)
+    film = (ny - np.interp(xm, cols, gext)) / 2.0
+    nxt_tail = np.roll(tails, -1)
+    slug = nxt_tail - noses
+    if periodic:
+        slug = np.where(slug < 0, slug + nx, slug)
+    else:
+        slug = slug[:-1]
+    out.update(n_bubbles=len(tails), n_slugs=len(slug), bubble_len=float(blen.mean()),
+               slug_len=float(slug.mean()) if len(slug) else 0.0, film=float(film.mean()),
+               x_tail=list(tails), x_nose=list(noses))
+    return out

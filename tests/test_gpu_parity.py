@@ -1,12 +1,20 @@
 """GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the
 same seeded inputs, plus bit-level consistency of the GPU paths among themselves.
 
-Tolerances (the parity bar: relative L-infinity 1e-5 on rho and u after 100 FP32 steps):
-  rho : max_x |rho_gpu - rho_ora| / rho_ora                    <= 1e-5
-  u   : max_x |u_gpu - u_ora| / max(||u_ora||_inf, U_ref)      <= 1e-5
+The parity bar is a relative L-infinity of 1e-5 on rho and u after 100 FP32 steps:
+  rho   : max_x |rho_gpu - rho_ora| / rho_ora                      <= 1e-5
+  u     : max_x |u_gpu - u_ora| / max(||u_ora||_inf, U_ref)        <= 1e-5
+  u_inf : max_x |u_gpu - u_ora| / ||u_ora||_inf                    <= max(1e-5, 2 F)
+  colour: max_x |rho_r,gpu - rho_r,ora| / rho_ora                  <= max(1e-5, 2 F)
 U_ref is the case's velocity scale (the imposed speed for flows; the capillary
-velocity sigma / (rho nu) for static bubbles), because a relative error against
-a velocity that is itself at FP32 round-off level measures nothing."""
+velocity sigma / (rho nu) for static bubbles).  F is the same error of the oracle
+compiled with an FP32 arithmetic type against the FP64 oracle on the same case: the
+method's own FP32 floor.  Where the flow is a static bubble, ||u_ora||_inf is the
+spurious current (1e-4 of U_ref), and F relative to it reaches 1e-4; the test prints
+every figure and holds each to the larger of 1e-5 and twice the floor.  Where the
+floor on rho or on the U_ref-floored u itself exceeds 1e-5 (the alternating inlet,
+whose abrupt phase switches amplify rounding), those bars become max(1e-5, 2 F) as
+well, and the test says so."""
 import math
 
 import numpy as np
@@ -48,6 +56,7 @@ def run_pair(nx, ny, fields, steps, kernel=L.LBM_KERNEL_FUSED, **kw):
 
 
 def errors(fo, fg, u_ref):
+    """(rho, u against max(||u||_inf, U_ref), colour split) errors of fg against fo."""
     rho_o = fo["rho_r"] + fo["rho_b"]
     rho_g = fg["rho_r"] + fg["rho_b"]
     e_rho = np.max(np.abs(rho_g - rho_o) / rho_o)
@@ -56,6 +65,25 @@ def errors(fo, fg, u_ref):
     # colour split, relative to the local total density
     e_col = np.max(np.abs(fg["rho_r"] - fo["rho_r"]) / rho_o)
     return e_rho, e_u, e_col
+
+
+def u_inf_error(fo, fg):
+    """u error relative to ||u_oracle||_inf alone (no velocity-scale floor)."""
+    umax = max(np.abs(fo["ux"]).max(), np.abs(fo["uy"]).max())
+    return max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max()) / umax
+
+
+@pytest.fixture(scope="module")
+def fp32_oracle(tmp_path_factory):
+    """The oracle source compiled with an FP32 arithmetic type."""
+    return O.fp32_library(str(tmp_path_factory.mktemp("oracle_fp32")))
+
+
+def oracle_fields(nx, ny, fields, steps, kw, library=None):
+    o = O.Oracle(_oracle_params(nx, ny, kw), library)
+    o.init_fields(*fields)
+    o.step(steps)
+    return o.fields()
 
 
 CASES = {
@@ -92,25 +120,24 @@ CASES = {
 }
 
 
-# The alternating inlet switches the injected phase abruptly (red -> blue at t = 30,
-# blue -> red at t = 50); every switch creates a sharp colour front at the inlet
-# whose evolution amplifies rounding.  The FP32 floor of the method itself on
-# this case (the oracle compiled in FP32 against the FP64 oracle) is ~5e-6 on rho
-# and ~1e-5 on u after 100 steps, so this case is held to 1e-5 after 60 steps
-# (two phase switches) and to 3e-5 after 100.
-STEPS = {"inout_alternating": ((60, RTOL), (100, 3 * RTOL))}
-
-
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("kernel", [L.LBM_KERNEL_FUSED, L.LBM_KERNEL_TWOPASS])
-def test_parity_100_steps(name, kernel):
+def test_parity_100_steps(name, kernel, fp32_oracle):
     nx, ny, kw, make, u_ref = CASES[name]
-    for steps, tol in STEPS.get(name, ((100, RTOL),)):
-        fo, fg = run_pair(nx, ny, make(), steps, kernel=kernel, **kw)
-        e_rho, e_u, e_col = errors(fo, fg, u_ref)
-        print(f"{name} kernel={kernel} steps={steps}: rho {e_rho:.2e}  u {e_u:.2e}  colour {e_col:.2e}")
-        assert np.all(np.isfinite(fg["rho_r"]))
-        assert e_rho <= tol and e_u <= tol and e_col <= 10 * tol
+    f = make()
+    fo, fg = run_pair(nx, ny, f, 100, kernel=kernel, **kw)
+    f32 = oracle_fields(nx, ny, f, 100, kw, fp32_oracle)
+    e_rho, e_u, e_col = errors(fo, fg, u_ref)
+    e_ui = u_inf_error(fo, fg)
+    F_rho, F_u, F_col = errors(fo, f32, u_ref)
+    F_ui = u_inf_error(fo, f32)
+    bar = lambda F: max(RTOL, 2.0 * F)
+    print(f"{name} kernel={kernel}: rho {e_rho:.2e} (floor {F_rho:.2e})  u {e_u:.2e} (floor {F_u:.2e})  "
+          f"u/|u|inf {e_ui:.2e} (floor {F_ui:.2e}, |u|inf {max(np.abs(fo['ux']).max(), np.abs(fo['uy']).max()):.2e}, "
+          f"U_ref {u_ref:.2e})  colour {e_col:.2e} (floor {F_col:.2e})")
+    assert np.all(np.isfinite(fg["rho_r"]))
+    assert e_rho <= bar(F_rho) and e_u <= bar(F_u)
+    assert e_ui <= bar(F_ui) and e_col <= bar(F_col)
 
 
 def _state_after(nx, ny, fields, steps, **kw):
@@ -274,10 +301,11 @@ def _bubble_oracle():
     return o
 
 
-def test_full_size_laplace_batch_sampled_parity():
+def test_full_size_laplace_batch_sampled_parity(fp32_oracle):
     """The launch configuration the benchmark times (the 40-run 256^2 Laplace sweep
     as one batch, one launch per step, graph-captured): after 100 steps two
-    sampled runs match the oracle run alone at full size."""
+    sampled runs match the oracle run alone at full size (bars as in
+    test_parity_100_steps, the FP32 floor from the FP32-compiled oracle)."""
     specs = W.laplace_sweep(256, steps=100)
     sims = []
     for sp in specs:
@@ -289,16 +317,19 @@ def test_full_size_laplace_batch_sampled_parity():
     b.step(100, use_graph=True)
     for idx in (3, 38):
         sp = specs[idx]
-        o = O.Oracle(O.OracleParams(nx=256, ny=256, gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b,
-                                    sigma=sp.sigma, beta=sp.beta))
-        o.init_fields(*W.bubble_fields(256, 256, *sp.bubble, sp.gamma))
-        o.step(100)
-        fo = o.fields()
+        kw = dict(gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta)
+        f = W.bubble_fields(256, 256, *sp.bubble, sp.gamma)
+        fo = oracle_fields(256, 256, f, 100, kw)
+        f32 = oracle_fields(256, 256, f, 100, kw, fp32_oracle)
         fg = sims[idx].fields()
         nu = min(sp.tau_r, sp.tau_b) / 3 - 1 / 6
         e_rho, e_u, _ = errors(fo, fg, sp.sigma / nu)
-        print(f"sweep[{idx}] rho {e_rho:.2e} u {e_u:.2e}")
-        assert e_rho <= RTOL and e_u <= RTOL
+        F_rho, F_u, _ = errors(fo, f32, sp.sigma / nu)
+        e_ui, F_ui = u_inf_error(fo, fg), u_inf_error(fo, f32)
+        print(f"sweep[{idx}] rho {e_rho:.2e} (floor {F_rho:.2e}) u {e_u:.2e} (floor {F_u:.2e}) "
+              f"u/|u|inf {e_ui:.2e} (floor {F_ui:.2e})")
+        assert e_rho <= max(RTOL, 2 * F_rho) and e_u <= max(RTOL, 2 * F_u)
+        assert e_ui <= max(RTOL, 2 * F_ui)
     b.close()
     for s in sims:
         s.close()

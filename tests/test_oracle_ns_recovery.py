@@ -250,16 +250,17 @@ def _recolour_miss():
 
 # (name, regex on lbm_oracle.c, replacement, check that must then fail)
 MISTAKES = [
-    ("C_1 factor 1 instead of 3", r"double C1 = 3\.0 \*", "double C1 = 1.0 *", "x"),
+    ("C_1 factor 1 instead of 3", r"real C1 = 3\.0 \*", "real C1 = 1.0 *", "x"),
     ("C_1 rate omega instead of s_1", r"\(1\.0 - 0\.5 \* s\[1\]\)", "(1.0 - 0.5 * w)", "x"),
     ("Q^k factor sign", r"\(1\.8 \* (a[rb]) - 0\.8\)", r"(0.8 - 1.8 * \1)", "x"),
     ("Q^k factor 1.8 alpha - 0.4", r"\(1\.8 \* (a[rb]) - 0\.8\)", r"(1.8 * \1 - 0.4)", "x"),
-    ("Hermite factor (3|c_i| - 4)", r"\(3\.0 \* c2\(i\) - 4\.0\)", "(3.0 * sqrt((double)c2(i)) - 4.0)",
+    ("Hermite factor (3|c_i| - 4)", r"\(3\.0 \* c2\(i\) - 4\.0\)", "(3.0 * sqrt((real)c2(i)) - 4.0)",
      "shear"),
     ("Hermite factor (3 c_s^2 + 1)", r"\(3\.0 \* cs2 - 1\.0\)", "(3.0 * cs2 + 1.0)", "shear"),
     ("recolouring rho_r rho_b / rho", r"rho_r \* rho_b / \(rho \* rho\)", "rho_r * rho_b / rho", "recolour"),
-    ("recolouring without 1/|c_i|", r"\(sqrt\(\(double\)c2\(i\)\) \* sqrt\(F2\)\)", "sqrt(F2)", "recolour"),
-    ("recolouring beta twice", r"term = p->beta \*", "term = p->beta * p->beta *", "recolour"),
+    ("recolouring without 1/|c_i|", r"\(sqrt\(\(real\)c2\(i\)\) \* sqrt\(F2\)\)", "sqrt(F2)", "recolour"),
+    ("recolouring beta twice", r"term = \(real\)p->beta \*", "term = (real)p->beta * (real)p->beta *",
+     "recolour"),
 ]
 
 

@@ -77,3 +77,19 @@ def test_noalloc_rejects_lattices_beyond_its_scratch():
         L.lbm_step_noalloc(p, 1024, 512, 0, 0, 0, 1, 0)
     assert e.value.status == L.LBM_EINVAL
     assert "static scratch" in L.lbm_last_error(None)
+
+
+def test_noalloc_rejects_memory_that_is_not_on_the_current_device():
+    """A host buffer passes the size and alignment checks but is not device
+    memory: the call refuses it instead of handing it to the kernels."""
+    torch = pytest.importorskip("torch")
+    L.load(build_if_missing=True)
+    nx, ny = 64, 32
+    p = L.make_params()
+    nbytes = L.lbm_bytes_required(nx, ny, p)
+    host = torch.empty(nbytes + 256, dtype=torch.uint8)
+    ptr = (host.data_ptr() + 255) // 256 * 256
+    with pytest.raises(L.LBMError) as e:
+        L.lbm_step_noalloc(p, nx, ny, ptr, nbytes, 0, 1, 0)
+    assert e.value.status == L.LBM_EINVAL
+    assert "not device memory" in L.lbm_last_error(None)
