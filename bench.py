@@ -10,10 +10,15 @@ CUDA graph.  One bench "step" = one LBM time step of all 40 lattices.
 
 Prints one JSON line.  `value` is whole-job MLUPS (million lattice-node
 updates per second, both colours of a node counting as one update) over the
-device-timed region (inputs resident in HBM).  `e2e` is the same metric through
-the public API with host buffers: upload of the initial fields, K steps and
-download of the final fields, all inside the timed region.  `--impl reference`
-times the FP64 CPU oracle on a bounded sample of the same workload.
+device-timed region (inputs resident in HBM).  That region replays the K-step
+graph R times back to back, R chosen so that it lasts at least 0.5 s (long
+enough for the nvidia-smi clock samples taken during it); `steps` is K,
+`timed_steps` R K.  `e2e` is the same metric through the public API with host
+buffers: upload of the initial fields, K steps and download of the final
+fields, all inside the timed region.  `per_dtype` repeats the device-timed sweep
+with FP16 and BF16 deviation storage and gives each storage type's error against
+the FP64 oracle on two sampled runs after 100 steps.  `--impl reference` times
+the FP64 CPU oracle (all host cores) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -35,15 +40,15 @@ sys.path.insert(0, ROOT)
 BYTES_PER_UPDATE = {0: 144, 1: 104, 2: 104}
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic of one k_step_fused launch on this workload from an ncu capture
-# (profiles/k_step_fused_laplace_sweep_40x256.md), valid only for the kernel
+# DRAM traffic of one k_step_fused launch on this workload from an ncu capture of
+# `dram__bytes_read.sum + dram__bytes_write.sum`, valid only for the kernel
 # sources with this hash; reported as null otherwise.
 NCU_TRAFFIC = {"sources_sha": "53264e91f9e3623d", "bytes_per_launch": 222819328 + 155179520}
 
 
 def kernel_sources_sha() -> str:
     h = hashlib.sha256()
-    for f in ("lbm_device.cuh", "lbm_kernels.cuh"):
+    for f in ("lbm_device.cuh", "lbm_kernels.cuh", "lbm_inst.cuh"):
         with open(os.path.join(ROOT, "paper_1903_01168_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -176,9 +181,20 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+def host_cores() -> int:
+    """Host cores this process may run on (the oracle's OpenMP threads)."""
+    n = os.environ.get("OMP_NUM_THREADS")
+    if n and n.isdigit():
+        return int(n)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def oracle_mlups(specs, steps: int, seconds: float):
     """FP64 oracle on a bounded sample: one sweep run at a time, `steps` steps each,
-    until `seconds` of CPU work have been spent.  Returns (MLUPS, sample text)."""
+    until `seconds` of wall time have been spent.  Returns (MLUPS, sample text)."""
     from oracle import oracle as O
     from paper_1903_01168_gb300 import workloads as W
     nodes = 0
@@ -195,7 +211,8 @@ def oracle_mlups(specs, steps: int, seconds: float):
         runs += 1
         if t_used >= seconds:
             break
-    return nodes / t_used / 1e6, f"{runs} of the 40 runs x {steps} steps on 256x256 (single-threaded C, FP64)"
+    return nodes / t_used / 1e6, (f"{runs} of the 40 runs x {steps} steps on 256x256 (plain C, FP64, "
+                                  f"rows split over {host_cores()} OpenMP threads)")
 
 
 def run_reference(args, rank, world):
@@ -218,31 +235,144 @@ def run_reference(args, rank, world):
         sims[j % len(sims)].step(1)
     dt = time.perf_counter() - t0
     mlups = 256 * 256 * args.steps / dt / 1e6
-    sample = f"each step = 1 time step of one 256x256 sweep run (rotating over 4 runs), FP64 oracle"
+    cores = host_cores()
+    sample = (f"each step = 1 time step of one 256x256 sweep run (rotating over 4 runs), FP64 oracle, "
+              f"{cores} OpenMP threads")
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "laplace_sweep_40x256x256_f32", "sample": sample},
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+STORAGE_NAMES = ["f32", "f16", "bf16"]
+
+
+class Sweep:
+    """The workload's lattices as one batch on `stream` (torch-owned memory),
+    with the plan tuned on the batch itself unless autotune is False."""
+
+    def __init__(self, L, specs, storage: int, stream, autotune: bool):
+        import torch
+        self.specs, self.storage, self.stream = specs, storage, stream
+        self.sims = []
+        with torch.cuda.stream(stream):
+            for sp in specs:
+                self.sims.append(L.Simulation(sp.nx, sp.ny, torch_memory=True, gamma=sp.gamma, tau_r=sp.tau_r,
+                                              tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta, storage=storage,
+                                              gx=sp.gx, bc_y=sp.bc_y))
+            self.init_all()
+            self.tuned, self.tune_s = None, 0.0
+            if autotune:
+                from paper_1903_01168_gb300.autotune import Autotuner
+                ta = time.perf_counter()
+                self.tuned = Autotuner().tune_batch(self.sims)
+                self.tune_s = time.perf_counter() - ta
+                self.init_all()
+                self.batch = L.Batch(self.sims, row_overhead=self.tuned["row_overhead"], plan=self.tuned["plan"],
+                                     member_plan_rows=self.tuned["member_plan_rows"])
+            else:
+                self.batch = L.Batch(self.sims)
+        self.nodes = sum(sp.nx * sp.ny for sp in specs)
+
+    def init_all(self):
+        for sp, s in zip(self.specs, self.sims):
+            if sp.geometry == "bubble":
+                s.init_bubble(*sp.bubble)
+            else:
+                s.init_slug(int(sp.slug[0]), sp.slug[1], sp.slug[2], True)
+
+    def timed(self, steps: int, warmup: int, floor_s: float, dist, local: int):
+        """Warm up, then time R back-to-back replays of the `steps`-step graph (R so
+        that the region lasts at least floor_s), between barriers, with CUDA events
+        on the launching stream and nvidia-smi clock samples.  Returns
+        (ms of the region, max over ranks; R; clock summary)."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.batch.step(warmup, use_graph=True)
+            self.batch.step(steps, use_graph=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(self.stream):
+            e0.record(self.stream)
+            self.batch.step(steps, use_graph=True)
+            e1.record(self.stream)
+        torch.cuda.synchronize()
+        one = max_over_ranks(e0.elapsed_time(e1), dist)
+        reps = max(1, int(-(-floor_s * 1e3 // max(one, 1e-3))))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            with torch.cuda.stream(self.stream):
+                e0.record(self.stream)
+                for _ in range(reps):
+                    self.batch.step(steps, use_graph=True)
+                e1.record(self.stream)
+            torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        return max_over_ranks(e0.elapsed_time(e1), dist), reps, clk.summary()
+
+    def close(self):
+        self.batch.close()
+        for s in self.sims:
+            s.close()
+
+
+_ORACLE_FIELDS = {}
+
+
+def sampled_oracle_error(L, specs, storage: int, idx=(3, 38), steps: int = 100):
+    """Relative L-inf error of rho and of u (against max(||u||_inf, sigma / nu)) of
+    sampled sweep runs after `steps` steps, GPU storage type `storage` against the
+    FP64 oracle, worst over the samples."""
+    from oracle import oracle as O
+    from paper_1903_01168_gb300 import workloads as W
+    import numpy as np
+    e_rho = e_u = 0.0
+    for i in idx:
+        sp = specs[i]
+        kw = dict(gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta)
+        f = W.bubble_fields(sp.nx, sp.ny, *sp.bubble, sp.gamma)
+        if (i, steps) not in _ORACLE_FIELDS:
+            o = O.Oracle(O.OracleParams(nx=sp.nx, ny=sp.ny, **kw))
+            o.init_fields(*f)
+            o.step(steps)
+            _ORACLE_FIELDS[(i, steps)] = o.fields()
+        fo = _ORACLE_FIELDS[(i, steps)]
+        with L.Simulation(sp.nx, sp.ny, storage=storage, **kw) as s:
+            s.init_fields(*f)
+            s.step(steps)
+            fg = s.fields()
+        ro = fo["rho_r"] + fo["rho_b"]
+        e_rho = max(e_rho, float(np.max(np.abs(fg["rho_r"] + fg["rho_b"] - ro) / ro)))
+        uref = max(np.abs(fo["ux"]).max(), np.abs(fo["uy"]).max(), sp.sigma / (min(sp.tau_r, sp.tau_b) / 3 - 1 / 6))
+        e_u = max(e_u, float(max(np.abs(fg["ux"] - fo["ux"]).max(), np.abs(fg["uy"] - fo["uy"]).max()) / uref))
+    return {"rho_rel_linf": e_rho, "u_rel_linf": e_u, "steps": steps,
+            "sample": f"sweep runs {list(idx)}, 256x256, vs the FP64 oracle"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--floor-seconds", type=float, default=0.5,
+                    help="shortest device-timed region: the K-step graph is replayed until it lasts this long")
     ap.add_argument("--workload", default="laplace_sweep", choices=["laplace_sweep", "ensemble", "serving"],
                     help="laplace_sweep: 40 x 256^2 (default); ensemble: 256 uneven lattices, FP16 "
                          "deviations; serving: Poisson-arrival open-channel requests")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+    ap.add_argument("--storage", default="f32", choices=STORAGE_NAMES,
                     help="population storage: FP32, or FP16 / BF16 deviations (FP32 arithmetic)")
+    ap.add_argument("--no-per-dtype", action="store_true", help="skip the FP16 / BF16 sweeps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the measured choice of plan_rows per size class (default plan)")
@@ -272,65 +402,23 @@ def main():
     L.load(build_if_missing=(rank == 0 and world == 1))
 
     specs = workload() if args.workload == "laplace_sweep" else ensemble_workload()
-    storage = {"f32": 0, "f16": 1, "bf16": 2}[args.storage]
+    storage = STORAGE_NAMES.index(args.storage)
     if args.workload == "ensemble":
         storage = 1   # the ensemble is defined with FP16-deviation storage
     stream = torch.cuda.Stream()
-    sim_params = [dict(gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b, sigma=sp.sigma, beta=sp.beta,
-                       storage=storage, gx=sp.gx, bc_y=sp.bc_y) for sp in specs]
-    sims = []
-    with torch.cuda.stream(stream):
-        for sp, kw in zip(specs, sim_params):
-            sims.append(L.Simulation(sp.nx, sp.ny, torch_memory=True, **kw))
-
-    def init_all():
-        for sp, s in zip(specs, sims):
-            if sp.geometry == "bubble":
-                s.init_bubble(*sp.bubble)
-            else:
-                s.init_slug(int(sp.slug[0]), sp.slug[1], sp.slug[2], True)
-
-    tuned = None
-    with torch.cuda.stream(stream):
-        init_all()
-        if not args.no_autotune:
-            # per size class plan_rows and plan options, timed on this batch, then a fresh start
-            from paper_1903_01168_gb300.autotune import Autotuner
-            ta = time.perf_counter()
-            tuned = Autotuner().tune_batch(sims)
-            tune_s = time.perf_counter() - ta
-            init_all()
-            batch = L.Batch(sims, row_overhead=tuned["row_overhead"], plan=tuned["plan"],
-                            member_plan_rows=tuned["member_plan_rows"])
-        else:
-            batch = L.Batch(sims)
-    nodes = sum(sp.nx * sp.ny for sp in specs)
+    peak, peak_kind = measured_peak()
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # warm-up (also captures the graphs of both lengths used below)
-    with torch.cuda.stream(stream):
-        batch.step(args.warmup, use_graph=True)
-        batch.step(args.steps, use_graph=True)
-    torch.cuda.synchronize()
-
-    # ---- device-timed region: K steps, inputs resident in HBM
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            ev0.record(stream)
-            batch.step(args.steps, use_graph=True)
-            ev1.record(stream)
-        torch.cuda.synchronize()
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    t_max = max_over_ranks(ms, dist)
-    mlups = job_mlups(nodes, args.steps, world, t_max * 1e-3)
-    ms_per_step = t_max / args.steps
+    # ---- device-timed region: R replays of the K-step graph, inputs resident in HBM
+    sw = Sweep(L, specs, storage, stream, not args.no_autotune)
+    nodes = sw.nodes
+    ms, reps, clocks = sw.timed(args.steps, args.warmup, args.floor_seconds, dist, local)
+    timed_steps = reps * args.steps
+    mlups = job_mlups(nodes, timed_steps, world, ms * 1e-3)
+    ms_per_step = ms / timed_steps
 
     # ---- end to end through the public API with host buffers
     host_fields = []
@@ -346,10 +434,10 @@ def main():
     torch.cuda.synchronize()
     te0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for s, f in zip(sims, host_fields):
+        for s, f in zip(sw.sims, host_fields):
             s.init_fields(*f)
-        batch.step(args.steps, use_graph=True)
-        outs = [s.fields() for s in sims]
+        sw.batch.step(args.steps, use_graph=True)
+        outs = [s.fields() for s in sw.sims]
     torch.cuda.synchronize()
     te = max_over_ranks(time.perf_counter() - te0, dist)
     algo_bytes = BYTES_PER_UPDATE[storage] * nodes
@@ -359,22 +447,43 @@ def main():
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "upload of initial fields + K steps + download of final fields, per step"}
     assert all(np.isfinite(o["rho_r"]).all() for o in outs)
+    tuned, tune_s, items = sw.tuned, sw.tune_s, sw.batch.items
+    sw.close()
 
-    peak, peak_kind = measured_peak()
     achieved = algo_bytes / (ms_per_step * 1e-3) / 1e9
     traffic = (NCU_TRAFFIC["bytes_per_launch"]
                if NCU_TRAFFIC["sources_sha"] == kernel_sources_sha() and storage == 0 else None)
+
+    # ---- the same sweep with every storage type, and each one's error against the oracle
+    per_dtype = None
+    if args.workload == "laplace_sweep" and not args.no_per_dtype:
+        per_dtype = {}
+        for st, name in enumerate(STORAGE_NAMES):
+            if st == storage:
+                m, ach = mlups, achieved
+            else:
+                sw2 = Sweep(L, specs, st, stream, not args.no_autotune)
+                ms2, reps2, _ = sw2.timed(args.steps, args.warmup, args.floor_seconds / 2, dist, local)
+                sw2.close()
+                m = job_mlups(nodes, reps2 * args.steps, world, ms2 * 1e-3)
+                ach = BYTES_PER_UPDATE[st] * nodes / (ms2 / (reps2 * args.steps) * 1e-3) / 1e9
+            per_dtype[name] = {"mlups": m, "bytes_per_update": BYTES_PER_UPDATE[st], "achieved_gbs": ach,
+                               "frac": ach / peak,
+                               "vs_oracle": sampled_oracle_error(L, specs, st) if rank == 0 else None}
+
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": (f"laplace_sweep_40x256x256_{args.storage}" if args.workload == "laplace_sweep"
-                                else "ensemble_256_uneven_f16dev"),
+        "warmup": args.warmup, "timed_steps": timed_steps, "graph_replays": reps,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if storage == 0 else STORAGE_NAMES[storage] + "-deviation (f32 math)",
+        "data": "synthetic",
+        "config": {"workload": (f"laplace_sweep_40x256x256_{STORAGE_NAMES[storage]}"
+                                if args.workload == "laplace_sweep" else "ensemble_256_uneven_f16dev"),
                    "lattices": len(specs), "nx": specs[0].nx if args.workload == "laplace_sweep" else "64..512",
                    "ny": specs[0].ny if args.workload == "laplace_sweep" else "64..1024",
-                   "nodes_per_step": nodes, "storage": ["f32", "f16", "bf16"][storage],
+                   "nodes_per_step": nodes, "storage": STORAGE_NAMES[storage],
                    "kernel": "k_step_fused (batched, graph)",
-                   "work_items": batch.items,
+                   "work_items": items,
                    "autotune": (None if tuned is None else
                                 {"seconds": round(tune_s, 2), "row_overhead": tuned["row_overhead"],
                                  "plan": {0: "auto", 1: "balanced", 2: "split"}[tuned["plan"]],
@@ -385,18 +494,18 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": algo_bytes},
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": args.steps + 1,
+        "gpu_launches": timed_steps + reps,
     }
+    if per_dtype is not None:
+        line["per_dtype"] = per_dtype
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "laplace_sweep":
         v, sample = oracle_mlups(specs, 100, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",
+                                "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    batch.close()
-    for s in sims:
-        s.close()
     if dist is not None:
         dist.destroy_process_group()
 

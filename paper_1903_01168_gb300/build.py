@@ -2,7 +2,8 @@
 
     python -m paper_1903_01168_gb300.build [--force] [--verbose]
 
-Produces ``paper_1903_01168_gb300/_native/liblbm_gb300.so`` from
+Produces ``paper_1903_01168_gb300/_native/liblbm_gb300.so`` (or the path in the
+environment variable LBM_GB300_LIB, which the binding then loads) from
 ``paper_1903_01168_gb300/csrc/*.cu`` and ``include/lbm.h``.  Each translation unit
 is compiled to an object in parallel (the step kernels of each storage type sit in
 their own units), then the objects are linked.  Rebuilds only when a source is
@@ -21,7 +22,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_native")
-LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
+LIB = os.environ.get("LBM_GB300_LIB") or os.path.join(OUT_DIR, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,8 +49,10 @@ def stale() -> bool:
 
 
 def compile_command(src: str, obj: str, extra: list[str] | None = None) -> list[str]:
+    """nvcc command for one unit; LBM_NVCC_FLAGS adds flags (e.g. -DLBM_FUSED_NSLOT=3)."""
+    env = os.environ.get("LBM_NVCC_FLAGS", "").split()
     return [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-            *(extra or []), "-c", "-o", obj, src]
+            *env, *(extra or []), "-c", "-o", obj, src]
 
 
 def link_command(objs: list[str], out: str) -> list[str]:
@@ -64,8 +67,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the library if needed and return its path."""
     if not force and not stale():
         return LIB
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    obj_dir = os.path.join(os.path.dirname(LIB), "obj")
     os.makedirs(obj_dir, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose else []
     srcs = sources()
     tag = f".{os.getpid()}"

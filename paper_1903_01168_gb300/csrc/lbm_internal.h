@@ -19,8 +19,11 @@ void host_set_global_error(const char *msg);
 
 // Launch shape of the fused kernel: columns per strip (= threads per block)
 // and shared-memory row slots per block.
+#ifndef LBM_FUSED_NSLOT
+#define LBM_FUSED_NSLOT 4
+#endif
 constexpr int FUSED_W = 128;
-constexpr int FUSED_NSLOT = 4;
+constexpr int FUSED_NSLOT = LBM_FUSED_NSLOT;
 
 // Launchers of the step kernels.  Each storage type T (float, __half,
 // __nv_bfloat16) is instantiated in its own translation units

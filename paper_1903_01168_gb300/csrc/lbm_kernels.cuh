@@ -22,6 +22,12 @@ namespace lbm {
 
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
+// Resident fused-kernel blocks per SM the register allocation is sized for
+// (0: the per-variant choice of FusedCfg::MINB).
+#ifndef LBM_FUSED_MIN_BLOCKS
+#define LBM_FUSED_MIN_BLOCKS 0
+#endif
+
 // ------------------------------------------------------------------ loaders
 
 // Stored values from global memory; ys is wrapped periodically.
@@ -197,9 +203,16 @@ struct FusedCfg {
     static constexpr int RING_BYTES = ((RING_FLOATS * 4 + 15) / 16) * 16;
     static constexpr int SMEM = DESC_BYTES + NSLOT * SLOT_BYTES + RING_BYTES + NSLOT * 8 + 16;
     static constexpr uint32_t TX_BYTES = (uint32_t)(NS * BOXW * 4 + DEV_BYTES);
+    // Blocks per SM the registers are sized for: 5 (96 registers) for FP32, 6 (80)
+    // for 16-bit storage, whose smaller rows let 6 blocks share the SM's shared
+    // memory; 4 (128) for MRT + Hermite, whose source term needs them.  Measured
+    // on the 40-lattice sweep: 4 -> 5 blocks +2.5 % (FP32), 4 -> 6 +7 % (FP16).
+    static constexpr int MINB = LBM_FUSED_MIN_BLOCKS > 0 ? LBM_FUSED_MIN_BLOCKS
+                                : (QRING ? 4 : (sizeof(T) == 4 ? 5 : 6));
     static_assert(BOXW <= 256, "TMA box dimension limit");
     static_assert((BOXW * sizeof(T)) % 16 == 0 && (BOXW * 4) % 16 == 0, "TMA inner box bytes");
     static_assert(G <= GMEM && G >= 3, "halo must cover the stencil and fit the memory ghost");
+    static_assert(NSLOT >= 4, "the prologue waits for rows ya-2 .. ya+1 before any slot is refilled");
 };
 
 // Persistent fused step.  Block b processes the work items
@@ -214,10 +227,10 @@ struct FusedCfg {
 // densities and e_i that the same thread pulled one iteration earlier (kept in
 // registers) and the colour field of rows y-1..y+1 in a shared ring (S2I4
 // gradient).  Stage B reads no source row, so a row's slot is refilled as soon
-// as stage A of the row above has used it.  One block runs 4 warps; 4 blocks
-// share an SM (128 registers per thread, shared memory per block below 56 KB).
+// as stage A of the row above has used it.  One block runs 4 warps; 5 or 6
+// blocks share an SM (FusedCfg::MINB).
 template <typename T, int CV, int W, int NSLOT>
-__global__ void __launch_bounds__(W, 4) k_step_fused(const SimDesc *__restrict__ descs,
+__global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_fused(const SimDesc *__restrict__ descs,
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ item_off, int n_blocks,
                                                      int step_offset, int *__restrict__ err) {

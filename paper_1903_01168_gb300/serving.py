@@ -105,7 +105,8 @@ def params_of(spec: SimSpec) -> L.lbm_params:
     kw = dict(gamma=spec.gamma, tau_r=spec.tau_r, tau_b=spec.tau_b, sigma=spec.sigma, beta=spec.beta,
               gx=spec.gx, gy=spec.gy, bc_x=spec.bc_x, bc_y=spec.bc_y, storage=spec.storage,
               u_in_r=spec.u_in_r, u_in_b=spec.u_in_b, p_out=spec.p_out,
-              inlet_period_r=spec.inlet_period_r, inlet_period_b=spec.inlet_period_b)
+              inlet_period_r=spec.inlet_period_r, inlet_period_b=spec.inlet_period_b,
+              collision=spec.collision, equilibrium=spec.equilibrium)
     return L.make_params(**kw)
 
 

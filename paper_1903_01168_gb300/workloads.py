@@ -145,6 +145,8 @@ class SimSpec:
     p_out: float = 0.0
     inlet_period_r: int = 0
     inlet_period_b: int = 0
+    collision: int = 0         # 0 BGK, 1 MRT
+    equilibrium: int = 0       # 0 standard, 1 Hermite (with the U^k source under MRT)
     extra: dict = field(default_factory=dict)
 
     def as_dict(self) -> dict:

@@ -1,8 +1,7 @@
 """Square-to-droplet resolution study (the paper's Sec. 4): workload recipe, the
 centreline Laplace error measure, and the oracle at 60 x 60.  The paper gives no
 viscosities, no steady-state time and no exact error norm, so its printed
-convergence orders are reported beside the measured ones (DESIGN) rather than
-pinned."""
+convergence orders are reported beside the measured ones rather than pinned."""
 import math
 
 import numpy as np
