@@ -154,30 +154,41 @@ def ensemble_workload():
     return W.ensemble(seed=W.DEFAULT_SEED, n_sims=256)
 
 
-def run_serving(args):
+def serving_trace_results(args) -> dict:
     """Serving trace: Poisson arrivals of open-channel slug requests (mixed lattice
     sizes, step counts and storage types) through the continuous-batching server,
     then the same trace one request at a time through the plain FP32 path."""
-    import torch
-    from paper_1903_01168_gb300 import lbm as L
     from paper_1903_01168_gb300 import serving as S
     from paper_1903_01168_gb300 import workloads as W
-    torch.cuda.set_device(0)
-    L.load(build_if_missing=True)
     trace = W.serving_trace(seed=W.DEFAULT_SEED, n_requests=args.requests, rate_hz=args.rate)
     # warm up kernels and graphs of every storage type
     warm = [(0.0, W.SimSpec(**{**sp.as_dict(), "nx": 256, "ny": 64, "steps": 64})) for _, sp in trace[:3]]
     S.Server(budget_bytes=150e9, chunk=32).run(warm)
     S.run_sequential(warm)
-    res_b, st_b = S.Server(budget_bytes=150e9, chunk=args.chunk).run(trace)
+    cap = None if args.active_nodes <= 0 else args.active_nodes
+    res_b, st_b = S.Server(budget_bytes=150e9, chunk=args.chunk, max_active_nodes=cap,
+                           priority=args.priority).run(trace)
     res_s, st_s = S.run_sequential(trace, storage=0)
-    line = {"metric": "MLUPS", "value": st_b["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serving_{args.requests}_requests_poisson_{args.rate}hz",
-                       "budget_bytes": 150e9, "chunk_steps": args.chunk},
-            "serving": {k: st_b[k] for k in ("requests", "p50_s", "p99_s", "mean_s", "makespan_s", "mlups")},
-            "sequential_f32": {k: st_s[k] for k in ("requests", "p50_s", "p99_s", "mean_s", "makespan_s",
-                                                     "mlups")}}
+    keys = ("requests", "p50_s", "p99_s", "mean_s", "makespan_s", "mlups")
+    return {"workload": f"serving_{args.requests}_requests_poisson_{args.rate}hz",
+            "trace": "open-channel slug requests, nx 512..8192, ny 64..256, 5k-50k steps, storage uniform over "
+                     "f32 / f16-deviation / bf16-deviation",
+            "budget_bytes": 150e9, "chunk_steps": args.chunk, "max_active_nodes": cap, "priority": args.priority,
+            "batched": {k: st_b[k] for k in keys}, "sequential_f32": {k: st_s[k] for k in keys},
+            "unstable_results": sum(1 for r in res_b if r.diag.get("nonfinite", 0))}
+
+
+def run_serving(args):
+    import torch
+    from paper_1903_01168_gb300 import lbm as L
+    torch.cuda.set_device(0)
+    L.load(build_if_missing=True)
+    sv = serving_trace_results(args)
+    line = {"metric": "MLUPS", "value": sv["batched"]["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
+            "config": {"workload": sv["workload"], "budget_bytes": 150e9, "chunk_steps": args.chunk,
+                       "max_active_nodes": sv["max_active_nodes"]},
+            "serving": sv["batched"], "sequential_f32": sv["sequential_f32"]}
     print(json.dumps(line), flush=True)
 
 
@@ -379,6 +390,11 @@ def main():
     ap.add_argument("--requests", type=int, default=24, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=1.5, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--chunk", type=int, default=500, help="serving: steps per batched chunk")
+    ap.add_argument("--active-nodes", type=int, default=8_000_000,
+                    help="serving: lattice nodes the active batch may hold (<= 0: no cap)")
+    ap.add_argument("--priority", default="arrival", choices=["arrival", "remaining_steps", "remaining_work"],
+                    help="serving: order in which resident requests enter the active batch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving trace in the default line")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -500,6 +516,8 @@ def main():
     }
     if per_dtype is not None:
         line["per_dtype"] = per_dtype
+    if rank == 0 and world == 1 and args.workload == "laplace_sweep" and not args.no_serving:
+        line["serving"] = serving_trace_results(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "laplace_sweep":
         v, sample = oracle_mlups(specs, 100, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",

@@ -123,9 +123,9 @@ typedef struct {
     int wall_slip;       /* walls (bc_y = WALL): 0 no slip (halfway bounce-back), 1 free
                             slip: diagonal populations travel on along the wall,
                             mirrored (Sec. 2.5 "Boundary conditions").  Free slip and a
-                            contact angle (below) run on the two-pass kernels: kernel
-                            FUSED is then LBM_EINVAL, AUTO takes TWOPASS, and such a
-                            lattice cannot join a batch */
+                            contact angle (below) select the wetting variant of the step
+                            kernels (fused or two-pass, alone or in a batch); the
+                            no-slip variant keeps fewer registers */
     double contact_angle;/* static contact angle on the walls, radians in (0, pi), measured
                             through the blue phase; 0 = no adjustment.  On the fluid rows
                             next to a wall the colour gradient is turned to the closer of

@@ -50,8 +50,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
+// Wetting walls: free-slip links or the contact-angle adjustment of F.
+bool wetting(const lbm_params *p) { return p->wall_slip != 0 || p->contact_angle > 0.0; }
+
 int variant_of(const lbm_params *p) {
-    return (p->collision == LBM_MRT ? CV_MRT : 0) | (p->equilibrium == LBM_EQ_HERMITE ? CV_HERMITE : 0);
+    return (p->collision == LBM_MRT ? CV_MRT : 0) | (p->equilibrium == LBM_EQ_HERMITE ? CV_HERMITE : 0) |
+           (wetting(p) ? CV_WET : 0);
 }
 
 }  // namespace
@@ -148,10 +152,6 @@ lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
     if (p->plan_rows < 0 || p->plan_rows > (1 << 20)) { set_err(err, "plan_rows out of range"); return LBM_EINVAL; }
     if (p->plan < LBM_PLAN_AUTO || p->plan > LBM_PLAN_SPLIT) { set_err(err, "unknown plan kind"); return LBM_EINVAL; }
     if (p->wall_slip != 0 && p->wall_slip != 1) { set_err(err, "wall_slip must be 0 or 1"); return LBM_EINVAL; }
-    if (p->kernel == LBM_KERNEL_FUSED && (p->wall_slip != 0 || p->contact_angle > 0.0)) {
-        set_err(err, "wetting walls run on the two-pass kernel (kernel AUTO or TWOPASS)");
-        return LBM_EINVAL;
-    }
     if (!(p->contact_angle >= 0.0 && p->contact_angle < 3.14159265358979)) {
         set_err(err, "contact_angle must be 0 (off) or in (0, pi) radians");
         return LBM_EINVAL;
@@ -463,8 +463,8 @@ cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, con
 // Resident fused blocks per SM for a storage type and collision variant
 // (occupancy query), times SMs.
 int resident_blocks(int storage, int variant) {
-    static int cache[3][4] = {};
-    if (storage < 0 || storage > 2 || variant < 0 || variant > 3) return 1;
+    static int cache[3][N_VARIANTS] = {};
+    if (storage < 0 || storage > 2 || variant < 0 || variant >= N_VARIANTS) return 1;
     if (cache[storage][variant]) return cache[storage][variant];
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -634,10 +634,7 @@ void slug_from_profile(const double *g, const double *pc, int nx, int ny, bool p
     if (ns > 0) o->slug_len = ss / ns;
 }
 
-// Wetting walls (free slip, contact angle) run on the two-pass kernels: the
-// fused kernel is compiled for no-slip walls only.
-bool wetting(const lbm_params *p) { return p->wall_slip != 0 || p->contact_angle > 0.0; }
-bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS && !wetting(&s->p); }
+bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS; }
 
 lbm_status sync_t0(lbm_sim *s) {
     if (s->dev_t0 != s->t) {
@@ -773,7 +770,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         }
     }
     const size_t nn = (size_t)nx * ny;
-    if ((p->kernel == LBM_KERNEL_TWOPASS || wetting(p)) &&
+    if (p->kernel == LBM_KERNEL_TWOPASS &&
         cudaMalloc(&s->d_aux, AUX_FIELDS * nn * sizeof(float)) != cudaSuccess) {
         set_err(s->err, "cudaMalloc of scratch field failed");
         return fail(LBM_ENOMEM);
@@ -1163,10 +1160,6 @@ lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts
             set_err(g_create_err, "batch members must exist and share a device");
             return LBM_EINVAL;
         }
-        if (wetting(&sims[i]->p)) {
-            set_err(g_create_err, "member %d has wetting walls (two-pass kernel only); batches run the fused kernel", i);
-            return LBM_EINVAL;
-        }
         strip_rows += (long long)((sims[i]->nx + FUSED_W - 1) / FUSED_W) * sims[i]->ny;
     }
     lbm_batch *b = new lbm_batch();
@@ -1183,7 +1176,7 @@ lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts
     // items grouped by (storage, variant): one launch per group and step
     std::vector<int> offs;
     for (int st = 0; st < 3; st++)
-        for (int cv = 0; cv < 4; cv++) {
+        for (int cv = 0; cv < N_VARIANTS; cv++) {
             std::vector<StripRef> strips;
             for (int i = 0; i < n; i++)
                 if (sims[i]->p.storage == st && sims[i]->h.variant == cv)

@@ -126,9 +126,12 @@ struct alignas(128) SimDesc {
 // Scratch field of the two-pass path: aux[5][ny][nx] = psi, rho_r, rho_b, q u_x, q u_y.
 constexpr int AUX_FIELDS = 5;
 
-// Collision variants (compile-time): bit 0 = MRT (else BGK), bit 1 = Hermite
-// equilibrium (with the U^k source when combined with MRT).
-constexpr int CV_MRT = 1, CV_HERMITE = 2;
+// Compile-time variants of the step kernels: bit 0 = MRT (else BGK), bit 1 =
+// Hermite equilibrium (with the U^k source when combined with MRT), bit 2 =
+// wetting walls (free-slip links and the contact-angle adjustment of F; without
+// it walls are no-slip and the fused kernel keeps fewer registers).
+constexpr int CV_MRT = 1, CV_HERMITE = 2, CV_WET = 4;
+constexpr int N_VARIANTS = 8;
 
 // One unit of work of a step launch: a strip of w <= W columns starting at x0,
 // marching over rows [ya, yb) of simulation `sim`.

@@ -1,0 +1,8 @@
+// lbm_fused_bf16_wet.cu -- the fused step kernel for BF16 deviation storage,
+// the four collision variants with wetting walls (free slip, contact angle).
+#include "lbm_inst.cuh"
+
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 4)
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 5)
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 6)
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 7)

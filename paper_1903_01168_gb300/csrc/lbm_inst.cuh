@@ -1,6 +1,6 @@
 // lbm_inst.cuh -- definitions of the step-kernel launchers declared in
-// lbm_internal.h.  Included by one small translation unit per storage type and
-// kernel family, which instantiates them with LBM_INSTANTIATE_FUSED(T) or
+// lbm_internal.h.  Included by small translation units that instantiate them
+// for one storage type: LBM_INSTANTIATE_FUSED(T, CV) per fused variant, or
 // LBM_INSTANTIATE_TWOPASS(T).
 #pragma once
 
@@ -17,24 +17,9 @@ const void *fused_kernel_cv() {
     return reinterpret_cast<const void *>(&k_step_fused<T, CV, FUSED_W, FUSED_NSLOT>);
 }
 
-template <typename T>
-const void *fused_kernel(int variant) {
-    switch (variant) {
-    case 0: return fused_kernel_cv<T, 0>();
-    case CV_MRT: return fused_kernel_cv<T, CV_MRT>();
-    case CV_HERMITE: return fused_kernel_cv<T, CV_HERMITE>();
-    default: return fused_kernel_cv<T, CV_MRT | CV_HERMITE>();
-    }
-}
-
-template <typename T>
-int fused_smem(int variant) {
-    switch (variant) {
-    case 0: return FusedCfg<T, 0, FUSED_W, FUSED_NSLOT>::SMEM;
-    case CV_MRT: return FusedCfg<T, CV_MRT, FUSED_W, FUSED_NSLOT>::SMEM;
-    case CV_HERMITE: return FusedCfg<T, CV_HERMITE, FUSED_W, FUSED_NSLOT>::SMEM;
-    default: return FusedCfg<T, CV_MRT | CV_HERMITE, FUSED_W, FUSED_NSLOT>::SMEM;
-    }
+template <typename T, int CV>
+int fused_smem_cv() {
+    return FusedCfg<T, CV, FUSED_W, FUSED_NSLOT>::SMEM;
 }
 
 template <typename T, int CV>
@@ -55,17 +40,6 @@ cudaError_t fused_launch_cv(const SimDesc *descs, const WorkItem *items, const i
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t fused_launch(int variant, const SimDesc *descs, const WorkItem *items, const int *item_off,
-                         int n_blocks, int off, int *err, cudaStream_t st) {
-    switch (variant) {
-    case 0: return fused_launch_cv<T, 0>(descs, items, item_off, n_blocks, off, err, st);
-    case CV_MRT: return fused_launch_cv<T, CV_MRT>(descs, items, item_off, n_blocks, off, err, st);
-    case CV_HERMITE: return fused_launch_cv<T, CV_HERMITE>(descs, items, item_off, n_blocks, off, err, st);
-    default: return fused_launch_cv<T, CV_MRT | CV_HERMITE>(descs, items, item_off, n_blocks, off, err, st);
-    }
-}
-
 template <typename T, int CV>
 cudaError_t twopass_launch_cv(const SimDesc *desc, int off, float *aux, long long nodes, cudaStream_t st) {
     const int g = (int)std::max<long long>(1, std::min<long long>((nodes + 255) / 256, 152LL * 16));
@@ -76,7 +50,7 @@ cudaError_t twopass_launch_cv(const SimDesc *desc, int off, float *aux, long lon
 
 template <typename T>
 cudaError_t twopass_launch(int variant, const SimDesc *desc, int off, float *aux, long long nodes, cudaStream_t st) {
-    switch (variant) {
+    switch (variant & (CV_MRT | CV_HERMITE)) {
     case 0: return twopass_launch_cv<T, 0>(desc, off, aux, nodes, st);
     case CV_MRT: return twopass_launch_cv<T, CV_MRT>(desc, off, aux, nodes, st);
     case CV_HERMITE: return twopass_launch_cv<T, CV_HERMITE>(desc, off, aux, nodes, st);
@@ -86,11 +60,11 @@ cudaError_t twopass_launch(int variant, const SimDesc *desc, int off, float *aux
 
 }  // namespace lbm
 
-#define LBM_INSTANTIATE_FUSED(T)                                                                                   \
-    template cudaError_t lbm::fused_launch<T>(int, const lbm::SimDesc *, const lbm::WorkItem *, const int *, int, \
-                                              int, int *, cudaStream_t);                                          \
-    template const void *lbm::fused_kernel<T>(int);                                                                \
-    template int lbm::fused_smem<T>(int);
+#define LBM_INSTANTIATE_FUSED(T, CV)                                                                            \
+    template cudaError_t lbm::fused_launch_cv<T, CV>(const lbm::SimDesc *, const lbm::WorkItem *, const int *, \
+                                                     int, int, int *, cudaStream_t);                           \
+    template const void *lbm::fused_kernel_cv<T, CV>();                                                        \
+    template int lbm::fused_smem_cv<T, CV>();
 
 #define LBM_INSTANTIATE_TWOPASS(T) \
     template cudaError_t lbm::twopass_launch<T>(int, const lbm::SimDesc *, int, float *, long long, cudaStream_t);

@@ -25,19 +25,55 @@ void host_set_global_error(const char *msg);
 constexpr int FUSED_W = 128;
 constexpr int FUSED_NSLOT = LBM_FUSED_NSLOT;
 
-// Launchers of the step kernels.  Each storage type T (float, __half,
-// __nv_bfloat16) is instantiated in its own translation units
-// (lbm_fused_*.cu, lbm_twopass_*.cu) so that they compile in parallel;
-// `variant` is the collision variant (bits CV_MRT, CV_HERMITE).
+// Launchers of the step kernels.  Each (storage type T, variant CV) pair of the
+// fused kernel is instantiated explicitly in its own translation unit group
+// (lbm_fused_*.cu: variants without and with wetting walls), and the two-pass
+// kernels of each T in lbm_twopass_*.cu, so that the units compile in parallel.
+template <typename T, int CV>
+cudaError_t fused_launch_cv(const SimDesc *descs, const WorkItem *items, const int *item_off, int n_blocks, int off,
+                            int *err, cudaStream_t st);
+template <typename T, int CV>
+const void *fused_kernel_cv();
+template <typename T, int CV>
+int fused_smem_cv();
+
+// Run-time dispatch over the variants (bits CV_MRT, CV_HERMITE, CV_WET).
+#define LBM_DISPATCH_CV(variant, CALL)          \
+    switch (variant) {                           \
+    case 0: CALL(0);                             \
+    case 1: CALL(1);                             \
+    case 2: CALL(2);                             \
+    case 3: CALL(3);                             \
+    case 4: CALL(4);                             \
+    case 5: CALL(5);                             \
+    case 6: CALL(6);                             \
+    default: CALL(7);                            \
+    }
+
 template <typename T>
 cudaError_t fused_launch(int variant, const SimDesc *descs, const WorkItem *items, const int *item_off,
-                         int n_blocks, int off, int *err, cudaStream_t st);
+                         int n_blocks, int off, int *err, cudaStream_t st) {
+#define LBM_CALL_(cv) return fused_launch_cv<T, cv>(descs, items, item_off, n_blocks, off, err, st)
+    LBM_DISPATCH_CV(variant, LBM_CALL_)
+#undef LBM_CALL_
+}
 template <typename T>
-const void *fused_kernel(int variant);
+const void *fused_kernel(int variant) {
+#define LBM_CALL_(cv) return fused_kernel_cv<T, cv>()
+    LBM_DISPATCH_CV(variant, LBM_CALL_)
+#undef LBM_CALL_
+}
 template <typename T>
-int fused_smem(int variant);
+int fused_smem(int variant) {
+#define LBM_CALL_(cv) return fused_smem_cv<T, cv>()
+    LBM_DISPATCH_CV(variant, LBM_CALL_)
+#undef LBM_CALL_
+}
+
 // Both passes of one two-pass step over `nodes` nodes of the descriptor at
-// `desc` (device memory), step `off` of a launch chunk, scratch `aux`.
+// `desc` (device memory), step `off` of a launch chunk, scratch `aux`.  The
+// two-pass kernels handle wetting walls in every variant (the CV_WET bit is
+// ignored).
 template <typename T>
 cudaError_t twopass_launch(int variant, const SimDesc *desc, int off, float *aux, long long nodes,
                            cudaStream_t st);

@@ -84,7 +84,7 @@ struct SmemLoader {
     const unsigned char *r0, *r1, *r2;
     int y, x0;
     SplitC q;
-    static constexpr int slip = 0;   // the fused kernel runs no free-slip lattices
+    int slip;   // free-slip walls (read only by the wetting variants' links)
     __device__ __forceinline__ const unsigned char *row(int ys) const {
         const int dy = ys - y;
         return dy < 0 ? r0 : (dy == 0 ? r1 : r2);
@@ -191,6 +191,8 @@ struct FusedCfg {
     static constexpr int SLOT_BYTES = ((RHO_BYTES + DEV_BYTES + 127) / 128) * 128;
     static constexpr int RING = W + 2;                       // ring width (columns x0-1 .. x0+W)
     static constexpr bool QRING = (CV & CV_MRT) && (CV & CV_HERMITE);
+    static constexpr bool WET = (CV & CV_WET) != 0;
+    static constexpr int LINKS = WET ? LINKS_ALL : LINKS_NOSLIP;
     // shared rings (floats) of what neighbouring threads read: psi and q u over
     // rows y-1..y+1.  Stage A of row y+1 may run while slower threads still do
     // stage B of row y-1, so they hold 4 rows.  The node's own rho_r, rho_b and
@@ -205,10 +207,11 @@ struct FusedCfg {
     static constexpr uint32_t TX_BYTES = (uint32_t)(NS * BOXW * 4 + DEV_BYTES);
     // Blocks per SM the registers are sized for: 5 (96 registers) for FP32, 6 (80)
     // for 16-bit storage, whose smaller rows let 6 blocks share the SM's shared
-    // memory; 4 (128) for MRT + Hermite, whose source term needs them.  Measured
+    // memory; 4 (128) for MRT + Hermite, whose source term needs them, and for
+    // wetting walls (free-slip links, contact-angle adjustment).  Measured
     // on the 40-lattice sweep: 4 -> 5 blocks +2.5 % (FP32), 4 -> 6 +7 % (FP16).
     static constexpr int MINB = LBM_FUSED_MIN_BLOCKS > 0 ? LBM_FUSED_MIN_BLOCKS
-                                : (QRING ? 4 : (sizeof(T) == 4 ? 5 : 6));
+                                : ((QRING || WET) ? 4 : (sizeof(T) == 4 ? 5 : 6));
     static_assert(BOXW <= 256, "TMA box dimension limit");
     static_assert((BOXW * sizeof(T)) % 16 == 0 && (BOXW * 4) % 16 == 0, "TMA inner box bytes");
     static_assert(G <= GMEM && G >= 3, "halo must cover the stencil and fit the memory ghost");
@@ -238,6 +241,8 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
     constexpr int G = Cfg::G, BOXW = Cfg::BOXW, RING = Cfg::RING;
     constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
     constexpr bool HERMITE_SRC = Cfg::QRING;
+    constexpr bool WET = Cfg::WET;
+    constexpr int LINKS = Cfg::LINKS;
     extern __shared__ __align__(128) unsigned char smem[];
 
     if ((int)blockIdx.x >= n_blocks) return;
@@ -339,6 +344,7 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             L.y = y;
             L.x0 = x0;
             L.q = qs;
+            L.slip = WET ? d.wet.slip : 0;
             return L;
         };
 
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
                     const int X = x0 - 1 + c;
                     const float ps = wall_psi(p, X, [&](int Xp) {
                         float rr, rb, jx, jy;
-                        pull_moments_rows<HERMITE, false, LINKS_NOSLIP>(p, L, Xp, Yn, t, rr, rb, jx, jy);
+                        pull_moments_rows<HERMITE, false, LINKS>(p, L, Xp, Yn, t, rr, rb, jx, jy);
                         return colour_field(p, rr, rb);
                     });
                     ring_psi[rs + c] = ps;
@@ -368,7 +374,7 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
                     const int c = tid + 1;
                     const int X = x0 + tid;
                     Pulled P;
-                    pull_node_rows<HERMITE, LINKS_NOSLIP>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                    pull_node_rows<HERMITE, LINKS>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
                     ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
                     out = P;
                     if (HERMITE_SRC) {
@@ -397,7 +403,7 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
                     int X = x0 - 1 + c;
                     if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
                     Pulled P;
-                    pull_node_rows<HERMITE, LINKS_NOSLIP>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+                    pull_node_rows<HERMITE, LINKS>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
                     ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
                     if (HERMITE_SRC) {
                         const NodeMoments m = node_moments(p, P);
@@ -425,6 +431,7 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             };
             float Fx, Fy, dQx = 0.0f, dQy = 0.0f;
             s2i4(ring(ring_psi), Fx, Fy);
+            if (WET) contact_angle_adjust(d.wet, p, y, Fx, Fy);
             if (HERMITE_SRC) {
                 float gx_, gy_;
                 s2i4(ring(ring_qx), dQx, gy_);

@@ -3,20 +3,25 @@
 A request is a simulation spec (lattice, physics, boundary conditions, storage
 type, number of steps) with an arrival time.  The server:
 
-  * keeps every admitted simulation resident in device memory until it is done;
-  * admits waiting requests in arrival order while the sum of the resident state
-    bytes stays within an HBM budget and the active lattice nodes stay within
-    `max_active_nodes`, about what it takes to keep every SM busy in one launch
-    (first come, first served: a request that does not fit blocks the ones
-    behind it).  Running more at once would only share the GPU among them and
-    delay every result;
-  * advances all resident simulations together, one batched fused-kernel launch
+  * admits arrived requests into device memory in arrival order while the sum
+    of the resident state bytes stays within an HBM budget; a request that does
+    not fit waits, and later ones that fit are admitted past it (backfill).
+    Admitted simulations stay resident until they are done;
+  * chooses the active set among the resident simulations: in arrival order,
+    while their lattice nodes stay within `max_active_nodes`, about what keeps
+    every SM busy in one launch, again letting later ones that fit pass one that
+    does not (the oldest always runs).  The members of a batch advance in
+    lockstep, one step per launch, so a batch larger than the GPU only slows every
+    member down: the cap keeps the GPU full while the oldest requests run at full
+    speed, close to first come first served, and small lattices that would leave
+    the GPU idle alone share it;
+  * advances the active simulations together, one batched fused-kernel launch
     per time step and storage type, replaying a graph of `graph_steps` steps; each
     simulation carries its own stop step, so one that finishes inside a chunk
     simply stops there while the others go on;
   * between chunks retires the finished simulations (their diagnostics are read
-    back), frees their memory and admits new arrivals, which therefore join work
-    already on the device.
+    back), frees their memory, admits new arrivals and recomputes the active set,
+    so new requests join work already on the device.
 
 `run_sequential` is the baseline: the same requests one at a time through the
 plain single-simulation FP32 path.  Both report the time from arrival to result
@@ -65,40 +70,53 @@ def state_bytes(spec: SimSpec) -> int:
 
 
 class Admission:
-    """First-come-first-served admission under a byte budget (host logic only)."""
+    """Admission into device memory under a byte budget (host logic only): in
+    arrival order, letting later requests that fit pass one that does not."""
 
-    def __init__(self, budget_bytes: int, max_active_nodes: int | None = None):
+    def __init__(self, budget_bytes: int):
         self.budget = int(budget_bytes)
         self.resident = 0
-        self.max_nodes = None if max_active_nodes is None else int(max_active_nodes)
-        self.active_nodes = 0
 
-    def fits(self, nbytes: int, nodes: int = 0) -> bool:
-        if self.resident + nbytes > self.budget:
-            return False
-        # the node cap never holds back a request when nothing is active
-        return self.max_nodes is None or self.active_nodes == 0 or self.active_nodes + nodes <= self.max_nodes
+    def fits(self, nbytes: int) -> bool:
+        return self.resident + nbytes <= self.budget
 
-    def take(self, waiting: deque, now: float, size_of, nodes_of=lambda r: 0) -> list:
-        """Pop and return the requests that have arrived by `now` and fit, in
-        arrival order, stopping at the first one that does not fit."""
-        out = []
-        while waiting and waiting[0].arrival <= now:
-            nb = size_of(waiting[0])
+    def take(self, waiting: deque, now: float, size_of) -> list:
+        """Remove from `waiting` and return, in arrival order, the requests that
+        have arrived by `now` and fit the budget, skipping those that do not."""
+        out, keep = [], deque()
+        while waiting:
+            r = waiting.popleft()
+            if r.arrival > now:
+                keep.append(r)
+                continue
+            nb = size_of(r)
             if nb > self.budget:
-                raise ValueError(f"request {waiting[0].rid} needs {nb} bytes, more than the whole budget")
-            nn = nodes_of(waiting[0])
-            if not self.fits(nb, nn):
-                break
-            self.resident += nb
-            self.active_nodes += nn
-            out.append(waiting.popleft())
+                raise ValueError(f"request {r.rid} needs {nb} bytes, more than the whole budget")
+            if self.fits(nb):
+                self.resident += nb
+                out.append(r)
+            else:
+                keep.append(r)
+        waiting.extend(keep)
         return out
 
-    def release(self, nbytes: int, nodes: int = 0):
+    def release(self, nbytes: int):
         self.resident -= int(nbytes)
-        self.active_nodes -= int(nodes)
-        assert self.resident >= 0 and self.active_nodes >= 0
+        assert self.resident >= 0
+
+
+def active_set(order: list, nodes_of, cap: int | None) -> list:
+    """The requests (ids in priority order) that run in the next chunk: in order,
+    while their nodes stay within `cap`, skipping one that would exceed it; the
+    first always runs, alone if it exceeds the cap by itself."""
+    act, tot = [], 0
+    for rid in order:
+        n = nodes_of(rid)
+        if act and cap is not None and tot + n > cap:
+            continue
+        act.append(rid)
+        tot += n
+    return act
 
 
 def params_of(spec: SimSpec) -> L.lbm_params:
@@ -141,10 +159,16 @@ def _stats(results: list[Result], makespan: float) -> dict:
 class Server:
     """Continuous-batching server on the current CUDA device."""
 
+    PRIORITIES = ("arrival", "remaining_steps", "remaining_work")
+
     def __init__(self, budget_bytes: float = 150e9, chunk: int = 500, max_chunk: int = 4000,
-                 graph_steps: int = 32, max_active_nodes: int | None = 8_000_000,
+                 graph_steps: int = 32, max_active_nodes: int | None = 8_000_000, priority: str = "arrival",
                  clock=time.perf_counter, sleep=time.sleep):
-        self.admission = Admission(int(budget_bytes), max_active_nodes)
+        if priority not in self.PRIORITIES:
+            raise ValueError(f"priority must be one of {self.PRIORITIES}")
+        self.priority = priority
+        self.admission = Admission(int(budget_bytes))
+        self.max_active_nodes = None if max_active_nodes is None else int(max_active_nodes)
         self.chunk = int(chunk)            # shortest chunk (bounds the wait of a new arrival)
         self.max_chunk = int(max_chunk)
         self.graph_steps = int(graph_steps)   # steps per graph replay (0: direct launches only)
@@ -153,40 +177,55 @@ class Server:
 
     def _chunk_len(self, active, waiting, now: float) -> int:
         """Run to the next completion, but no longer than max_chunk; only `chunk`
-        steps while the next request has not arrived yet (it may fit when it
+        steps while the next request has not arrived yet (it may join when it
         does).  A request that has arrived and still waits is held back by the
-        budget or the node cap, which only a completion relieves."""
+        budget or the active cap, which only a completion relieves."""
         left = min(r.spec.steps - s.t for s, r, _, _ in active.values())
         n = max(1, min(left, self.max_chunk))
-        if waiting and waiting[0].arrival > now:
+        if waiting and min(q.arrival for q in waiting) > now:
             n = min(n, self.chunk)
         return n
+
+    def _rank(self, entry, rid: int):
+        """Sort key of a resident request for the active set: its arrival (oldest
+        first), its remaining steps (most first: members of one batch advance in
+        lockstep, so a request with many steps left finishes last), or its
+        remaining work in node updates (least first)."""
+        s, r = entry[0], entry[1]
+        if self.priority == "remaining_steps":
+            return (-(r.spec.steps - s.t), r.arrival, rid)
+        if self.priority == "remaining_work":
+            return ((r.spec.steps - s.t) * r.spec.nx * r.spec.ny, r.arrival, rid)
+        return (r.arrival, rid)
 
     def run(self, trace: list[tuple[float, SimSpec]]) -> tuple[list[Result], dict]:
         reqs = [Request(i, a, sp) for i, (a, sp) in enumerate(trace)]
         waiting = deque(sorted(reqs, key=lambda r: r.arrival))
-        active: dict[int, tuple] = {}          # rid -> (sim, request, admitted_at, bytes)
+        resident: dict[int, tuple] = {}        # rid -> (sim, request, admitted_at, bytes)
         results: list[Result] = []
         batch = None
         members: tuple = ()
         t0 = self.clock()
-        while waiting or active:
+        while waiting or resident:
             now = self.clock() - t0
-            for r in self.admission.take(waiting, now, lambda q: state_bytes(q.spec),
-                                         lambda q: q.spec.nx * q.spec.ny):
+            for r in self.admission.take(waiting, now, lambda q: state_bytes(q.spec)):
                 s = start_simulation(r.spec)
                 s.set_stop(r.spec.steps)
-                active[r.rid] = (s, r, now, state_bytes(r.spec))
-            if not active:
-                self.sleep(max(0.0, waiting[0].arrival - (self.clock() - t0)))
+                resident[r.rid] = (s, r, now, state_bytes(r.spec))
+            if not resident:
+                self.sleep(max(0.0, min(q.arrival for q in waiting) - (self.clock() - t0)))
                 continue
-            key = tuple(sorted(active))
+            order = sorted(resident, key=lambda k: self._rank(resident[k], k))
+            key = tuple(sorted(active_set(order, lambda k: resident[k][1].spec.nx * resident[k][1].spec.ny,
+                                          self.max_active_nodes)))
             if key != members:
                 if batch is not None:
                     batch.close()
-                batch = L.Batch([active[k][0] for k in key])
+                batch = L.Batch([resident[k][0] for k in key])
                 members = key
-            n = self._chunk_len(active, waiting, self.clock() - t0)
+            active = {k: resident[k] for k in key}
+            pending = list(waiting) + [resident[k][1] for k in resident if k not in active]
+            n = self._chunk_len(active, deque(q for q in pending if q.arrival > now), self.clock() - t0)
             g = self.graph_steps
             if g > 0 and n >= g:
                 # one graph of g steps per batch, replayed; the remainder launched directly
@@ -209,9 +248,9 @@ class Server:
                 batch = None
                 members = ()
                 for k in retired:
-                    s, r, adm, nb = active.pop(k)
+                    s, r, adm, nb = resident.pop(k)
                     s.close()
-                    self.admission.release(nb, r.spec.nx * r.spec.ny)
+                    self.admission.release(nb)
         if batch is not None:
             batch.close()
         makespan = self.clock() - t0

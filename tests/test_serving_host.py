@@ -4,7 +4,7 @@ from collections import deque
 
 import pytest
 
-from paper_1903_01168_gb300.serving import Admission, Request
+from paper_1903_01168_gb300.serving import Admission, Request, active_set
 from paper_1903_01168_gb300.workloads import SimSpec, serving_trace
 
 
@@ -14,35 +14,30 @@ def _req(rid, arrival, nbytes):
     return r
 
 
-def test_admits_in_arrival_order_within_budget():
+def test_admits_in_arrival_order_within_budget_with_backfill():
     a = Admission(100)
-    q = deque([_req(0, 0.0, 40), _req(1, 0.1, 50), _req(2, 0.2, 20), _req(3, 5.0, 1)])
+    q = deque([_req(0, 0.0, 40), _req(1, 0.1, 50), _req(2, 0.2, 20), _req(3, 0.3, 10), _req(4, 5.0, 1)])
     got = a.take(q, now=1.0, size_of=lambda r: r.nbytes)
-    assert [r.rid for r in got] == [0, 1]          # 2 would exceed 100, and blocks 3 behind it
-    assert a.resident == 90 and [r.rid for r in q] == [2, 3]
+    assert [r.rid for r in got] == [0, 1, 3]       # 2 would exceed 100; 3 fits and passes it
+    assert a.resident == 100 and [r.rid for r in q] == [2, 4]
     assert a.take(q, now=1.0, size_of=lambda r: r.nbytes) == []
     a.release(40)                                   # request 0 retires
     got = a.take(q, now=1.0, size_of=lambda r: r.nbytes)
-    assert [r.rid for r in got] == [2]              # 3 has not arrived yet
+    assert [r.rid for r in got] == [2]              # 4 has not arrived yet
     got = a.take(q, now=6.0, size_of=lambda r: r.nbytes)
-    assert [r.rid for r in got] == [3] and a.resident == 71
+    assert [r.rid for r in got] == [4] and a.resident == 81
 
 
-def test_active_node_cap_holds_back_later_requests():
-    a = Admission(1000, max_active_nodes=100)
-    q = deque([_req(0, 0.0, 1), _req(1, 0.0, 1), _req(2, 0.0, 1)])
-    nodes = {0: 60, 1: 50, 2: 30}
-    got = a.take(q, now=0.0, size_of=lambda r: r.nbytes, nodes_of=lambda r: nodes[r.rid])
-    assert [r.rid for r in got] == [0]              # 60 + 50 > 100, and FCFS keeps 2 behind 1
-    a.release(1, 60)
-    got = a.take(q, now=0.0, size_of=lambda r: r.nbytes, nodes_of=lambda r: nodes[r.rid])
-    assert [r.rid for r in got] == [1, 2] and a.active_nodes == 80
+def test_active_set_keeps_the_oldest_and_backfills_to_the_cap():
+    nodes = {0: 60, 1: 50, 2: 30, 3: 200, 4: 5}
+    assert active_set([0, 1, 2], nodes.get, 100) == [0, 2]       # 1 would exceed; 2 fits after 0
+    assert active_set([3, 0, 4], nodes.get, 100) == [3]          # the oldest runs alone when it exceeds the cap
+    assert active_set([0, 3, 4], nodes.get, 100) == [0, 4]
+    assert active_set([0, 1, 2], nodes.get, None) == [0, 1, 2]   # no cap: everything resident runs
 
 
 def test_node_cap_never_blocks_an_idle_server():
-    a = Admission(1000, max_active_nodes=10)
-    got = a.take(deque([_req(0, 0.0, 1)]), now=0.0, size_of=lambda r: r.nbytes, nodes_of=lambda r: 500)
-    assert [r.rid for r in got] == [0]
+    assert active_set([0], {0: 500}.get, 10) == [0]
 
 
 def test_request_larger_than_budget_is_an_error():
