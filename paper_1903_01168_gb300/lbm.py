@@ -238,8 +238,16 @@ def lbm_time(sim: int) -> int:
     return load().lbm_time(sim)
 
 
-def lbm_read_fields(sim: int, nx: int, ny: int) -> dict:
-    out = {k: np.empty((ny, nx)) for k in ("rho_r", "rho_b", "ux", "uy", "p")}
+def lbm_read_fields(sim: int, nx: int, ny: int, out: dict | None = None) -> dict:
+    """Fields into `out` (C-contiguous float64 arrays (ny, nx) keyed rho_r, rho_b, ux,
+    uy, p, e.g. views of pinned host memory) or into new arrays."""
+    names = ("rho_r", "rho_b", "ux", "uy", "p")
+    if out is None:
+        out = {k: np.empty((ny, nx)) for k in names}
+    for k in names:
+        a = out[k]
+        if a.dtype != np.float64 or a.shape != (ny, nx) or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"out[{k!r}] must be a C-contiguous float64 array of shape {(ny, nx)}")
     _check(load().lbm_read_fields(sim, *[_dptr(out[k]) for k in ("rho_r", "rho_b", "ux", "uy", "p")]), sim)
     return out
 
@@ -430,8 +438,10 @@ class Simulation:
     def synchronize(self):
         lbm_synchronize(self.h)
 
-    def fields(self) -> dict:
-        return lbm_read_fields(self.h, self.nx, self.ny)
+    def fields(self, out: dict | None = None) -> dict:
+        """rho_r, rho_b, ux, uy, p as float64 (ny, nx) arrays; `out` gives the arrays
+        to fill (pinned host memory makes the device-to-host copies direct)."""
+        return lbm_read_fields(self.h, self.nx, self.ny, out)
 
     def populations(self) -> np.ndarray:
         """Pre-collision populations, array (2, 9, ny, nx)."""
