@@ -1,0 +1,6 @@
+// lbm_fused_bf16_wet_hermite.cu -- the fused step kernel for BF16 split-form deviation storage:
+// BGK and MRT with the Hermite equilibrium and wetting walls.
+#include "lbm_inst.cuh"
+
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 6)
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 7)

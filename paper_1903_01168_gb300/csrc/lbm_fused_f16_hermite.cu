@@ -1,0 +1,6 @@
+// lbm_fused_f16_hermite.cu -- the fused step kernel for FP16 split-form deviation storage: BGK
+// and MRT with the Hermite equilibrium and no-slip walls, both march directions.
+#include "lbm_inst.cuh"
+
+LBM_INSTANTIATE_FUSED(__half, 2)
+LBM_INSTANTIATE_FUSED(__half, 3)

@@ -14,7 +14,7 @@ namespace lbm {
 
 template <typename T, int CV>
 const void *fused_kernel_cv() {
-    return reinterpret_cast<const void *>(&k_step_fused<T, CV, FUSED_W, FUSED_NSLOT>);
+    return reinterpret_cast<const void *>(&k_step_fused<T, CV, FUSED_W, FUSED_NSLOT, 1>);
 }
 
 template <typename T, int CV>
@@ -29,15 +29,30 @@ cudaError_t fused_launch_cv(const SimDesc *descs, const WorkItem *items, const i
     static bool attr_done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
+    // the downward kernel is compiled only where some step uses it
+    constexpr bool DOWN = LBM_FUSED_ALTERNATE != 0;
+    auto up = k_step_fused<T, CV, FUSED_W, FUSED_NSLOT, 1>;
+    auto down = k_step_fused<T, CV, FUSED_W, FUSED_NSLOT, DOWN ? -1 : 1>;
     if (dev < 64 && !attr_done[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(fused_kernel_cv<T, CV>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM);
+        cudaError_t e = cudaFuncSetAttribute(up, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e == cudaSuccess && DOWN) e = cudaFuncSetAttribute(down, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
-    k_step_fused<T, CV, FUSED_W, FUSED_NSLOT><<<n_blocks, FUSED_W, SMEM, st>>>(descs, items, item_off, n_blocks, off,
-                                                                                err);
-    return cudaGetLastError();
+    // programmatic dependent launch: the launch of step j+1 overlaps the tail of
+    // step j; the kernel waits for its prerequisites before its first access
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_blocks);
+    cfg.blockDim = dim3(FUSED_W);
+    cfg.dynamicSmemBytes = SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = LBM_FUSED_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const bool march_down = LBM_FUSED_ALTERNATE == 2 || (LBM_FUSED_ALTERNATE == 1 && (off & 1));
+    return cudaLaunchKernelEx(&cfg, march_down ? down : up, descs, items, item_off, n_blocks, off, err);
 }
 
 template <typename T, int CV>

@@ -27,6 +27,15 @@ constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 #ifndef LBM_FUSED_MIN_BLOCKS
 #define LBM_FUSED_MIN_BLOCKS 0
 #endif
+// 1: each fused step is launched as a programmatic dependent of the previous one.
+#ifndef LBM_FUSED_PDL
+#define LBM_FUSED_PDL 1
+#endif
+// March direction of the fused steps: 0 every step up, 1 consecutive steps in
+// opposite directions, 2 every step down.
+#ifndef LBM_FUSED_ALTERNATE
+#define LBM_FUSED_ALTERNATE 0
+#endif
 
 // ------------------------------------------------------------------ loaders
 
@@ -232,11 +241,17 @@ struct FusedCfg {
 // gradient).  Stage B reads no source row, so a row's slot is refilled as soon
 // as stage A of the row above has used it.  One block runs 4 warps; 5 or 6
 // blocks share an SM (FusedCfg::MINB).
-template <typename T, int CV, int W, int NSLOT>
+//
+// DIR = +1 marches up (rows ya .. yb-1), DIR = -1 down (yb-1 .. ya); every node
+// is computed the same way in both.  Consecutive steps march in opposite
+// directions, so that a step starts on the rows the previous one wrote last,
+// while they are still in L2.
+template <typename T, int CV, int W, int NSLOT, int DIR>
 __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_fused(const SimDesc *__restrict__ descs,
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ item_off, int n_blocks,
                                                      int step_offset, int *__restrict__ err) {
+    static_assert(DIR == 1 || DIR == -1, "march direction");
     using Cfg = FusedCfg<T, CV, W, NSLOT>;
     constexpr int G = Cfg::G, BOXW = Cfg::BOXW, RING = Cfg::RING;
     constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
@@ -245,6 +260,12 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
     constexpr int LINKS = Cfg::LINKS;
     extern __shared__ __align__(128) unsigned char smem[];
 
+    // Launched as a programmatic dependent of the previous step: the next step's
+    // blocks may become resident while this one drains, and this block touches no
+    // memory that earlier work writes (descriptors, state, error word) before
+    // every prerequisite grid has completed and its writes are visible.
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if ((int)blockIdx.x >= n_blocks) return;
     const int tid = threadIdx.x;
 
@@ -298,11 +319,14 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             if (tid == 0) atomicOr(err, ERR_BADITEM);
             continue;
         }
-        const int row_first = ya - 2, row_last = yb + 1;
+        const int row_first = ya - 2, row_last = yb + 1, n_rows = row_last - row_first + 1;
+        // march index of source row r: the order in which rows are loaded
+        auto mi = [&](int r) { return DIR > 0 ? r - row_first : row_last - r; };
+        auto row_at = [&](int m) { return DIR > 0 ? row_first + m : row_last - m; };
 
         auto row_valid = [&](int r) { return !wall_y || (r >= 0 && r < ny); };
-        auto slot_of = [&](int r) { return (r - row_first) % NSLOT; };
-        auto parity_of = [&](int r) { return (uint32_t)(((r - row_first) / NSLOT) & 1); };
+        auto slot_of = [&](int r) { return mi(r) % NSLOT; };
+        auto parity_of = [&](int r) { return (uint32_t)((mi(r) / NSLOT) & 1); };
         auto row_ptr = [&](int r) { return slots + slot_of(r) * Cfg::SLOT_BYTES; };
         // Load source row r (both colour densities and all 16 deviation planes,
         // columns x0-G .. x0+W+G-1) into its slot.  A row behind a wall is not
@@ -322,14 +346,14 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             tma_load_2d(dst, &gd->tmap_rho, &bars[s], xb, brow * Cfg::NS);
             tma_load_2d(dst + Cfg::RHO_BYTES, &gd->tmap_dev, &bars[s], xb, brow * 16);
         };
-        int next_issue = row_first;   // meaningful on thread 0 only
+        int next_m = 0;   // march index of the next row to load; meaningful on thread 0 only
         if (tid == 0) {
-            for (; next_issue <= row_last && next_issue < row_first + NSLOT; ++next_issue) issue(next_issue);
+            for (; next_m < n_rows && next_m < NSLOT; ++next_m) issue(row_at(next_m));
         }
 
         bool ok = true;
         auto wait_row = [&](int r) {
-            if (ok && r <= row_last && row_valid(r)) {
+            if (ok && mi(r) < n_rows && row_valid(r)) {
                 if (!mbar_wait_bounded(&bars[slot_of(r)], parity_of(r), WAIT_LIMIT_CYCLES)) {
                     ok = false;
                     s_bad = 1;
@@ -443,27 +467,30 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             NodeStore<T>(d, p, bdst, x, y).put(P.rr, P.rb, dr, db, sm, sgx, sgy);
         };
 
-        // prologue: ring rows ya and ya - 1
-        wait_row(ya - 1);
-        wait_row(ya);
-        wait_row(ya + 1);
-        Pulled Pc, Pn;   // pulled state of this thread's node in rows y and y + 1
-        stageA(ya, Pc);
-        wait_row(ya - 2);
-        stageA(ya - 1, Pn);
-        __syncthreads();   // rows < ya are no longer read: refill their slots
+        // prologue: ring rows y0 and y0 - DIR, y0 the first row collided
+        const int y0 = DIR > 0 ? ya : yb - 1;
+        wait_row(y0 - 1);
+        wait_row(y0);
+        wait_row(y0 + 1);
+        Pulled Pc, Pn;   // pulled state of this thread's node in rows y and y + DIR
+        stageA(y0, Pc);
+        wait_row(y0 - 2 * DIR);
+        stageA(y0 - DIR, Pn);
+        __syncthreads();   // rows behind y0 are no longer read: refill their slots
         if (tid == 0) {
-            for (; next_issue <= row_last && next_issue <= ya - 1 + NSLOT; ++next_issue) issue(next_issue);
+            for (; next_m < n_rows && next_m <= mi(y0 - DIR) + NSLOT; ++next_m) issue(row_at(next_m));
         }
 
-        for (int y = ya; y < yb; ++y) {
-            wait_row(y + 2);
-            stageA(y + 1, Pn);
+        for (int k = 0; k < yb - ya; ++k) {
+            const int y = y0 + DIR * k;
+            wait_row(y + 2 * DIR);
+            stageA(y + DIR, Pn);
             __syncthreads();
             if (s_bad) break;
             if (tid == 0) {
-                // rows <= y are no longer read (stage A(y+1) was their last reader)
-                for (; next_issue <= row_last && next_issue <= y + NSLOT; ++next_issue) issue(next_issue);
+                // row y and those behind it are no longer read (stage A(y + DIR)
+                // was their last reader)
+                for (; next_m < n_rows && next_m <= mi(y) + NSLOT; ++next_m) issue(row_at(next_m));
             }
             stageB(y, Pc);
             Pc = Pn;
@@ -477,10 +504,10 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
                 // that none lands after the block's shared memory is released: the
                 // latest phase issued into each slot covers the earlier ones
                 for (int s = 0; s < NSLOT; s++) {
-                    int last = -1 << 30;
-                    for (int r = row_first; r < next_issue; ++r)
-                        if (slot_of(r) == s) last = r;
-                    if (last > (-1 << 30)) mbar_wait_bounded(&bars[s], parity_of(last), WAIT_LIMIT_CYCLES / 4);
+                    int last = -1;
+                    for (int m = 0; m < next_m; ++m)
+                        if (m % NSLOT == s) last = m;
+                    if (last >= 0) mbar_wait_bounded(&bars[s], (uint32_t)((last / NSLOT) & 1), WAIT_LIMIT_CYCLES / 4);
                 }
             }
             __syncthreads();

@@ -4,10 +4,15 @@ x viscosity ratio {1, 10} x sigma {0.001, 0.01}, beta 0.7) after 20 000 steps.
 Calls only the oracle and the seeded workload recipes.
 
     OMP_NUM_THREADS=1 python tests/golden/make_laplace_sweep.py [--procs 8] [--steps 20000]
+    OMP_NUM_THREADS=1 python tests/golden/make_laplace_sweep.py --fp32
 
 Per run: the Laplace jump dp and R_eff (mean p inside r < R_eff/2 minus mean p
 outside r > R_eff + 8, R_eff from the light-phase area), the largest spurious
-speed max |u|, and the colour masses at t = 0 and at the end."""
+speed max |u|, and the colour masses at t = 0 and at the end.
+
+--fp32 adds "runs_fp32" to the existing file: the same runs with the oracle
+compiled with an FP32 arithmetic type (oracle.fp32_library), i.e. what FP32
+rounding alone does to each result over 20 000 steps."""
 import argparse
 import json
 import multiprocessing as mp
@@ -19,15 +24,25 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 
 
+_FP32_LIB = None
+
+
 def run_one(args):
-    idx, steps = args
+    idx, steps, fp32 = args
     sys.path.insert(0, ROOT)
+    import tempfile
     import numpy as np
     from oracle import oracle as O
     from paper_1903_01168_gb300 import workloads as W
+    global _FP32_LIB
+    library = None
+    if fp32:
+        if _FP32_LIB is None:
+            _FP32_LIB = O.fp32_library(tempfile.mkdtemp(prefix="orc32_"))
+        library = _FP32_LIB
     sp = W.laplace_sweep(256, steps=steps)[idx]
     o = O.Oracle(O.OracleParams(nx=sp.nx, ny=sp.ny, gamma=sp.gamma, tau_r=sp.tau_r, tau_b=sp.tau_b,
-                                sigma=sp.sigma, beta=sp.beta))
+                                sigma=sp.sigma, beta=sp.beta), library=library)
     o.init_fields(*W.bubble_fields(sp.nx, sp.ny, *sp.bubble, sp.gamma))
     f0 = o.fields()
     t0 = time.time()
@@ -48,13 +63,21 @@ def main():
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--out", default=os.path.join(HERE, "laplace_sweep_20000.json"))
+    ap.add_argument("--fp32", action="store_true", help="add the FP32-compiled oracle's runs to --out")
     a = ap.parse_args()
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     ctx = mp.get_context("spawn")
     with ctx.Pool(a.procs) as pool:
-        res = dict(pool.map(run_one, [(i, a.steps) for i in range(40)], chunksize=1))
-    out = {"source": "FP64 oracle (oracle/lbm_oracle.c), tests/golden/make_laplace_sweep.py",
-           "steps": a.steps, "lattice": [256, 256], "beta": 0.7, "runs": [res[i] for i in range(40)]}
+        res = dict(pool.map(run_one, [(i, a.steps, a.fp32) for i in range(40)], chunksize=1))
+    if a.fp32:
+        with open(a.out) as f:
+            out = json.load(f)
+        assert out["steps"] == a.steps
+        out["runs_fp32"] = [res[i] for i in range(40)]
+        out["source_fp32"] = "the same oracle source compiled with ORC_REAL=float (oracle.fp32_library)"
+    else:
+        out = {"source": "FP64 oracle (oracle/lbm_oracle.c), tests/golden/make_laplace_sweep.py",
+               "steps": a.steps, "lattice": [256, 256], "beta": 0.7, "runs": [res[i] for i in range(40)]}
     with open(a.out, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", a.out)
