@@ -55,7 +55,7 @@ bool wetting(const lbm_params *p) { return p->wall_slip != 0 || p->contact_angle
 
 int variant_of(const lbm_params *p) {
     return (p->collision == LBM_MRT ? CV_MRT : 0) | (p->equilibrium == LBM_EQ_HERMITE ? CV_HERMITE : 0) |
-           (wetting(p) ? CV_WET : 0);
+           (wetting(p) ? CV_WET : 0) | (p->bc_x == LBM_BC_INOUT ? CV_OPEN : 0);
 }
 
 }  // namespace
@@ -76,6 +76,7 @@ struct lbm_sim {
     WorkItem *d_items = nullptr;
     int *d_off = nullptr;        // per-block item ranges of the plan
     int n_items = 0, n_blocks = 0;
+    int launch_flags = 0;   // fused-kernel flags of the plan (FUSED_EARLY_NEXT)
     int *d_err = nullptr;
     float *d_aux = nullptr;      // two-pass scratch field
     double *d_part = nullptr;    // diagnostic partials + final
@@ -97,7 +98,7 @@ struct lbm_batch {
     int n_items = 0;
     // one launch per (storage, variant) group: items [item0, ...) and block
     // ranges off[off0 .. off0 + blocks]
-    struct Group { int storage, variant, item0, off0, blocks; };
+    struct Group { int storage, variant, item0, off0, blocks, flags; };
     std::vector<Group> groups;
     // groups beyond the first run concurrently on their own streams (fork / join)
     std::vector<cudaStream_t> gstreams;
@@ -163,7 +164,11 @@ lbm_status validate(int nx, int ny, const lbm_params *p, char *err) {
     return LBM_OK;
 }
 
-constexpr int GHOST = 8;   // ghost columns kept on each side of a row
+// Ghost columns kept on each side of a row: one 32-byte sector of FP32 values,
+// so that the interior columns and the periodic copies are stored in whole
+// sectors (a 16-byte FP32 ghost moved less DRAM but put every row's stores off
+// the sector grid and measured 4 % slower).
+constexpr int GHOST = 8;
 
 int pitch_rho(int nx) { return (nx + 2 * GHOST + 3) / 4 * 4; }   // 16-byte rows of floats
 
@@ -300,6 +305,21 @@ struct Plan {
     std::vector<int> off;   // block b owns items [off[b], off[b+1])
     int blocks = 0;
 };
+
+// Launch flags for a plan run as the only launch of each step: a plan of one
+// piece per block, all of the same width and within one row of the same
+// height, lets the next step launch early (its blocks then land on whichever
+// SMs free first, which only matters where the pieces differ).
+int plan_flags(const Plan &P, bool only_launch) {
+    if (!only_launch || P.items.empty() || (int)P.items.size() != P.blocks) return 0;
+    int lo = 1 << 30, hi = 0, w0 = P.items[0].w;
+    for (const WorkItem &it : P.items) {
+        if (it.w != w0) return 0;
+        lo = std::min(lo, it.yb - it.ya);
+        hi = std::max(hi, it.yb - it.ya);
+    }
+    return hi - lo <= 1 ? FUSED_EARLY_NEXT : 0;
+}
 
 constexpr int MIN_PIECE = 8;   // default shortest row range worth a 4-row halo
 constexpr double DEFAULT_ROW_OVERHEAD = 1.0;   // fixed cost of a strip row, in busy warps
@@ -452,11 +472,11 @@ Plan make_plan(const std::vector<StripRef> &strips, int kind, int rows_per_item,
 }
 
 cudaError_t launch_fused_any(int storage, int variant, const SimDesc *descs, const WorkItem *items,
-                             const int *item_off, int n_blocks, int off, int *err, cudaStream_t st) {
+                             const int *item_off, int n_blocks, int off, int flags, int *err, cudaStream_t st) {
     switch (storage) {
-    case ST_F32: return fused_launch<float>(variant, descs, items, item_off, n_blocks, off, err, st);
-    case ST_F16DEV: return fused_launch<__half>(variant, descs, items, item_off, n_blocks, off, err, st);
-    default: return fused_launch<__nv_bfloat16>(variant, descs, items, item_off, n_blocks, off, err, st);
+    case ST_F32: return fused_launch<float>(variant, descs, items, item_off, n_blocks, off, flags, err, st);
+    case ST_F16DEV: return fused_launch<__half>(variant, descs, items, item_off, n_blocks, off, flags, err, st);
+    default: return fused_launch<__nv_bfloat16>(variant, descs, items, item_off, n_blocks, off, flags, err, st);
     }
 }
 
@@ -659,7 +679,7 @@ lbm_status step_direct(lbm_sim *s, long n) {
     for (long j = 0; j < n; j++) {
         if (use_fused(s)) {
             CK(launch_fused_any(s->p.storage, s->h.variant, s->d_desc, s->d_items, s->d_off, s->n_blocks, (int)j,
-                                s->d_err, s->stream));
+                                s->launch_flags, s->d_err, s->stream));
         } else {
             CK(launch_twopass(s, (int)j));
         }
@@ -760,6 +780,7 @@ lbm_status create_common(int nx, int ny, const lbm_params *p, void *buf, size_t 
         Plan P = make_plan(strips, p->plan, 0, resident_blocks(p->storage, variant_of(p)), DEFAULT_ROW_OVERHEAD);
         s->n_items = (int)P.items.size();
         s->n_blocks = P.blocks;
+        s->launch_flags = plan_flags(P, true);
         if (cudaMalloc(&s->d_items, P.items.size() * sizeof(WorkItem)) != cudaSuccess ||
             cudaMalloc(&s->d_off, P.off.size() * sizeof(int)) != cudaSuccess ||
             cudaMemcpy(s->d_items, P.items.data(), P.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) !=
@@ -1173,7 +1194,9 @@ lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts
         b->t_mirror.push_back(sims[i]->t);
         b->t_stop.push_back(sims[i]->h.t_end);
     }
-    // items grouped by (storage, variant): one launch per group and step
+    // items grouped by (storage, variant): one launch per group and step, each
+    // planned for all resident blocks (splitting the blocks between the groups'
+    // concurrent launches in proportion to their cost measured 1.8x slower)
     std::vector<int> offs;
     for (int st = 0; st < 3; st++)
         for (int cv = 0; cv < N_VARIANTS; cv++) {
@@ -1184,12 +1207,14 @@ lbm_status lbm_batch_create_ex(lbm_sim *const *sims, int n, const lbm_batch_opts
                               opts->member_plan_rows ? opts->member_plan_rows[i] : sims[i]->p.plan_rows);
             if (strips.empty()) continue;
             Plan P = make_plan(strips, opts->plan, rows_per_item, resident_blocks(st, cv), row_overhead);
-            lbm_batch::Group g{st, cv, (int)items.size(), (int)offs.size(), P.blocks};
+            lbm_batch::Group g{st, cv, (int)items.size(), (int)offs.size(), P.blocks, plan_flags(P, true)};
             for (int &o : P.off) o += g.item0;
             items.insert(items.end(), P.items.begin(), P.items.end());
             offs.insert(offs.end(), P.off.begin(), P.off.end());
             b->groups.push_back(g);
         }
+    if (b->groups.size() > 1)   // concurrent launch groups: no early launch of the next step
+        for (auto &g : b->groups) g.flags = 0;
     b->n_items = (int)items.size();
     if (cudaMalloc(&b->d_descs, n * sizeof(SimDesc)) != cudaSuccess ||
         cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess ||
@@ -1254,7 +1279,7 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
             if (gi > 0) CK(cudaStreamWaitEvent(st, b->fork, 0));
             for (long j = 0; j < k; j++)
                 CK(launch_fused_any(g.storage, g.variant, b->d_descs, b->d_items, b->d_off + g.off0, g.blocks, (int)j,
-                                    b->d_err, st));
+                                    g.flags, b->d_err, st));
             if (gi > 0) {
                 CK(cudaEventRecord(b->gjoin[gi - 1], st));
                 CK(cudaStreamWaitEvent(b->stream, b->gjoin[gi - 1], 0));

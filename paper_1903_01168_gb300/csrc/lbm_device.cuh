@@ -129,9 +129,15 @@ constexpr int AUX_FIELDS = 5;
 // Compile-time variants of the step kernels: bit 0 = MRT (else BGK), bit 1 =
 // Hermite equilibrium (with the U^k source when combined with MRT), bit 2 =
 // wetting walls (free-slip links and the contact-angle adjustment of F; without
-// it walls are no-slip and the fused kernel keeps fewer registers).
-constexpr int CV_MRT = 1, CV_HERMITE = 2, CV_WET = 4;
-constexpr int N_VARIANTS = 8;
+// it walls are no-slip and the fused kernel keeps fewer registers), bit 3 =
+// inlet / outlet columns in x (else periodic in x).  The fused kernel of a
+// periodic lattice carries no open-column code: its mere presence in the loop
+// cost the periodic sweep 2 %.
+constexpr int CV_MRT = 1, CV_HERMITE = 2, CV_WET = 4, CV_OPEN = 8;
+constexpr int N_VARIANTS = 16;
+// Launch flag of the fused kernel: the next step may launch as soon as this one
+// starts (plans of equal pieces, one launch per step).
+constexpr int FUSED_EARLY_NEXT = 1;
 
 // One unit of work of a step launch: a strip of w <= W columns starting at x0,
 // marching over rows [ya, yb) of simulation `sim`.

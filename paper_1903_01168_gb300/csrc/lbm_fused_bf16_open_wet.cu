@@ -1,0 +1,6 @@
+// lbm_fused_bf16_open_wet.cu -- the fused step kernel for BF16 split-form deviation storage: BGK
+// and MRT with the standard equilibrium, wetting walls and inlet / outlet columns.
+#include "lbm_inst.cuh"
+
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 12)
+LBM_INSTANTIATE_FUSED(__nv_bfloat16, 13)

@@ -1,5 +1,5 @@
 // lbm_fused_bf16_wet_hermite.cu -- the fused step kernel for BF16 split-form deviation storage:
-// BGK and MRT with the Hermite equilibrium and wetting walls.
+// BGK and MRT with the Hermite equilibrium and wetting walls, periodic in x.
 #include "lbm_inst.cuh"
 
 LBM_INSTANTIATE_FUSED(__nv_bfloat16, 6)

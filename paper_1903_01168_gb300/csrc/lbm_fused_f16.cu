@@ -1,6 +1,6 @@
 // lbm_fused_f16.cu -- the fused step kernel for FP16 split-form deviation storage: BGK and MRT with
-// the standard equilibrium and no-slip walls, both march directions (one small
-// translation unit per storage type and variant pair, compiled in parallel).
+// the standard equilibrium and no-slip walls, periodic in x (one
+// small translation unit per storage type and variant pair, compiled in parallel).
 #include "lbm_inst.cuh"
 
 LBM_INSTANTIATE_FUSED(__half, 0)

@@ -1,5 +1,5 @@
 // lbm_fused_f16_hermite.cu -- the fused step kernel for FP16 split-form deviation storage: BGK
-// and MRT with the Hermite equilibrium and no-slip walls, both march directions.
+// and MRT with the Hermite equilibrium and no-slip walls, periodic in x.
 #include "lbm_inst.cuh"
 
 LBM_INSTANTIATE_FUSED(__half, 2)

@@ -1,0 +1,6 @@
+// lbm_fused_f16_open_wet_hermite.cu -- the fused step kernel for FP16 split-form deviation storage:
+// BGK and MRT with the Hermite equilibrium, wetting walls and inlet / outlet columns.
+#include "lbm_inst.cuh"
+
+LBM_INSTANTIATE_FUSED(__half, 14)
+LBM_INSTANTIATE_FUSED(__half, 15)

@@ -1,0 +1,6 @@
+// lbm_fused_f32_open_wet.cu -- the fused step kernel for FP32 deviation storage: BGK
+// and MRT with the standard equilibrium, wetting walls and inlet / outlet columns.
+#include "lbm_inst.cuh"
+
+LBM_INSTANTIATE_FUSED(float, 12)
+LBM_INSTANTIATE_FUSED(float, 13)

@@ -24,7 +24,7 @@ int fused_smem_cv() {
 
 template <typename T, int CV>
 cudaError_t fused_launch_cv(const SimDesc *descs, const WorkItem *items, const int *item_off, int n_blocks, int off,
-                            int *err, cudaStream_t st) {
+                            int flags, int *err, cudaStream_t st) {
     constexpr int SMEM = FusedCfg<T, CV, FUSED_W, FUSED_NSLOT>::SMEM;
     static bool attr_done[64] = {false};
     int dev = 0;
@@ -52,7 +52,7 @@ cudaError_t fused_launch_cv(const SimDesc *descs, const WorkItem *items, const i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const bool march_down = LBM_FUSED_ALTERNATE == 2 || (LBM_FUSED_ALTERNATE == 1 && (off & 1));
-    return cudaLaunchKernelEx(&cfg, march_down ? down : up, descs, items, item_off, n_blocks, off, err);
+    return cudaLaunchKernelEx(&cfg, march_down ? down : up, descs, items, item_off, n_blocks, off, flags, err);
 }
 
 template <typename T, int CV>
@@ -77,7 +77,7 @@ cudaError_t twopass_launch(int variant, const SimDesc *desc, int off, float *aux
 
 #define LBM_INSTANTIATE_FUSED(T, CV)                                                                            \
     template cudaError_t lbm::fused_launch_cv<T, CV>(const lbm::SimDesc *, const lbm::WorkItem *, const int *, \
-                                                     int, int, int *, cudaStream_t);                           \
+                                                     int, int, int, int *, cudaStream_t);                      \
     template const void *lbm::fused_kernel_cv<T, CV>();                                                        \
     template int lbm::fused_smem_cv<T, CV>();
 

@@ -29,15 +29,16 @@ constexpr int FUSED_NSLOT = LBM_FUSED_NSLOT;
 // fused kernel is instantiated explicitly in its own translation unit group
 // (lbm_fused_*.cu: variants without and with wetting walls), and the two-pass
 // kernels of each T in lbm_twopass_*.cu, so that the units compile in parallel.
+// `flags`: FUSED_EARLY_NEXT lets the next step launch as soon as this one starts.
 template <typename T, int CV>
 cudaError_t fused_launch_cv(const SimDesc *descs, const WorkItem *items, const int *item_off, int n_blocks, int off,
-                            int *err, cudaStream_t st);
+                            int flags, int *err, cudaStream_t st);
 template <typename T, int CV>
 const void *fused_kernel_cv();
 template <typename T, int CV>
 int fused_smem_cv();
 
-// Run-time dispatch over the variants (bits CV_MRT, CV_HERMITE, CV_WET).
+// Run-time dispatch over the variants (bits CV_MRT, CV_HERMITE, CV_WET, CV_OPEN).
 #define LBM_DISPATCH_CV(variant, CALL)          \
     switch (variant) {                           \
     case 0: CALL(0);                             \
@@ -47,13 +48,21 @@ int fused_smem_cv();
     case 4: CALL(4);                             \
     case 5: CALL(5);                             \
     case 6: CALL(6);                             \
-    default: CALL(7);                            \
+    case 7: CALL(7);                             \
+    case 8: CALL(8);                             \
+    case 9: CALL(9);                             \
+    case 10: CALL(10);                           \
+    case 11: CALL(11);                           \
+    case 12: CALL(12);                           \
+    case 13: CALL(13);                           \
+    case 14: CALL(14);                           \
+    default: CALL(15);                           \
     }
 
 template <typename T>
 cudaError_t fused_launch(int variant, const SimDesc *descs, const WorkItem *items, const int *item_off,
-                         int n_blocks, int off, int *err, cudaStream_t st) {
-#define LBM_CALL_(cv) return fused_launch_cv<T, cv>(descs, items, item_off, n_blocks, off, err, st)
+                         int n_blocks, int off, int flags, int *err, cudaStream_t st) {
+#define LBM_CALL_(cv) return fused_launch_cv<T, cv>(descs, items, item_off, n_blocks, off, flags, err, st)
     LBM_DISPATCH_CV(variant, LBM_CALL_)
 #undef LBM_CALL_
 }

@@ -250,21 +250,26 @@ template <typename T, int CV, int W, int NSLOT, int DIR>
 __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_fused(const SimDesc *__restrict__ descs,
                                                      const WorkItem *__restrict__ items,
                                                      const int *__restrict__ item_off, int n_blocks,
-                                                     int step_offset, int *__restrict__ err) {
+                                                     int step_offset, int flags, int *__restrict__ err) {
     static_assert(DIR == 1 || DIR == -1, "march direction");
     using Cfg = FusedCfg<T, CV, W, NSLOT>;
     constexpr int G = Cfg::G, BOXW = Cfg::BOXW, RING = Cfg::RING;
     constexpr bool HERMITE = (CV & CV_HERMITE) != 0;
     constexpr bool HERMITE_SRC = Cfg::QRING;
     constexpr bool WET = Cfg::WET;
+    constexpr bool OPEN = (CV & CV_OPEN) != 0;
     constexpr int LINKS = Cfg::LINKS;
     extern __shared__ __align__(128) unsigned char smem[];
 
-    // Launched as a programmatic dependent of the previous step: the next step's
-    // blocks may become resident while this one drains, and this block touches no
-    // memory that earlier work writes (descriptors, state, error word) before
-    // every prerequisite grid has completed and its writes are visible.
-    asm volatile("griddepcontrol.launch_dependents;");
+    // Launched as a programmatic dependent of the previous step: this block
+    // touches no memory that earlier work writes (descriptors, state, error word)
+    // before every prerequisite grid has completed and its writes are visible.
+    // With FUSED_EARLY_NEXT (plans of equal pieces, one launch per step) the next
+    // step may launch at once, its blocks waiting in the slots this grid frees;
+    // otherwise only once this block's work is done (below): on uneven batches
+    // and concurrent launch groups the early trigger placed waiting blocks on SMs
+    // in the order slots freed and cost 5-16 %.
+    if (flags & FUSED_EARLY_NEXT) asm volatile("griddepcontrol.launch_dependents;");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if ((int)blockIdx.x >= n_blocks) return;
     const int tid = threadIdx.x;
@@ -372,9 +377,26 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             return L;
         };
 
+        auto rs_of = [&](int Y) { return ((Y + 4) & 3) * RING; };   // ring row of lattice row Y
+        // ring column c (0 or w+1) of row Y by one thread's full pull (next to
+        // walls and open columns, or where the node also needs q u)
+        auto edge_full = [&](const auto &L, int Y, int c) {
+            int X = x0 - 1 + c;
+            if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
+            Pulled P;
+            pull_node_rows<HERMITE, LINKS>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
+            ring_psi[rs_of(Y) + c] = colour_field(p, P.rr, P.rb);
+            if (HERMITE_SRC) {
+                const NodeMoments m = node_moments(p, P);
+                const float q = p.q_r * m.rr + p.q_b * m.rb;
+                ring_qx[rs_of(Y) + c] = q * m.ux;
+                ring_qy[rs_of(Y) + c] = q * m.uy;
+            }
+        };
+
         // stage A: ring row Y, columns x0-1 .. x0+w
         auto stageA = [&](int Y, Pulled &out) {
-            const int rs = ((Y + 4) & 3) * RING;
+            const int rs = rs_of(Y);
             if (wall_y && (Y < 0 || Y >= ny)) {
                 const int Yn = Y < 0 ? 0 : ny - 1;
                 const auto L = loader(Yn);
@@ -410,31 +432,56 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
                 }
                 // the two edge columns x0-1 and x0+w only need psi (and q u): the
                 // last warp computes them 16 lanes per node, unless a boundary
-                // touches them (open column, wall row) or the node needs q u
+                // touches them (wall row) or the node needs q u
                 const int Ye = Y < 0 ? Y + ny : (Y >= ny ? Y - ny : Y);
-                const bool edge_plain = !HERMITE_SRC && !(wall_y && (Ye == 0 || Ye == ny - 1)) &&
-                                        (p.bc_x == BC_PERIODIC || (x0 - 1 >= 1 && x0 + w <= nx - 2));
-                if (edge_plain) {
-                    if (tid >= W - 32) {
-                        const int lane = tid & 31, e = lane >> 4;
-                        const int X = e == 0 ? x0 - 1 : x0 + w;
-                        float rr, rb;
-                        pull_rho_coop16(p, L, X, Y, lane & 15, rr, rb);
-                        if ((lane & 15) == 0) ring_psi[rs + (e == 0 ? 0 : w + 1)] = colour_field(p, rr, rb);
+                const bool wall_row = wall_y && (Ye == 0 || Ye == ny - 1);
+                if constexpr (!OPEN) {
+                    // bc_x is always periodic here (the variant says so); the
+                    // run-time test stays because without it the compiler lays
+                    // out this loop 0.9 % slower on the periodic sweep (measured)
+                    if (p.bc_x != BC_PERIODIC) {
+                    } else if (!HERMITE_SRC && !wall_row) {
+                        if (tid >= W - 32) {
+                            const int lane = tid & 31, e = lane >> 4;
+                            const int X = e == 0 ? x0 - 1 : x0 + w;
+                            float rr, rb;
+                            pull_rho_coop16(p, L, X, Y, lane & 15, rr, rb);
+                            if ((lane & 15) == 0) ring_psi[rs + (e == 0 ? 0 : w + 1)] = colour_field(p, rr, rb);
+                        }
+                    } else if (tid < 2) {
+                        edge_full(L, Y, tid == 0 ? 0 : w + 1);
                     }
-                } else if (tid < 2) {
-                    const int c = tid == 0 ? 0 : w + 1;
-                    int X = x0 - 1 + c;
-                    if (p.bc_x == BC_INOUT) X = X < 0 ? 0 : (X >= nx ? nx - 1 : X);
-                    Pulled P;
-                    pull_node_rows<HERMITE, LINKS>(p, L, X, Y, t, false, 0.0f, 0.0f, P);
-                    ring_psi[rs + c] = colour_field(p, P.rr, P.rb);
-                    if (HERMITE_SRC) {
-                        const NodeMoments m = node_moments(p, P);
-                        const float q = p.q_r * m.rr + p.q_b * m.rb;
-                        ring_qx[rs + c] = q * m.ux;
-                        ring_qy[rs + c] = q * m.uy;
+                } else {
+                    // open lattice: a side beyond the inlet (x = -1) or the outlet
+                    // (x = nx) takes the values of the open column itself (zero
+                    // gradient, the pull clamps X there), copied by the thread that
+                    // wrote that column; the edge next to an open column (x = 0 or
+                    // nx - 1, whose pull is the Zou-He one) is pulled in full
+                    const bool open_l = x0 == 0, open_r = x0 + w == nx;
+                    const int cc = (open_l && tid == 0) ? 0 : ((open_r && tid == w - 1) ? w + 1 : -1);
+                    if (cc >= 0) {
+                        ring_psi[rs + cc] = ring_psi[rs + tid + 1];
+                        if (HERMITE_SRC) {
+                            ring_qx[rs + cc] = ring_qx[rs + tid + 1];
+                            ring_qy[rs + cc] = ring_qy[rs + tid + 1];
+                        }
                     }
+                    const bool plain_l = !open_l && x0 - 1 >= 1, plain_r = !open_r && x0 + w <= nx - 2;
+                    if (!HERMITE_SRC && !wall_row && (plain_l || plain_r)) {
+                        if (tid >= W - 32) {
+                            // all 32 lanes take part (full-warp shuffles); a side
+                            // that is not plain pulls column x0 and discards it
+                            const int lane = tid & 31, e = lane >> 4;
+                            const bool plain = e == 0 ? plain_l : plain_r;
+                            const int X = plain ? (e == 0 ? x0 - 1 : x0 + w) : x0;
+                            float rr, rb;
+                            pull_rho_coop16(p, L, X, Y, lane & 15, rr, rb);
+                            if ((lane & 15) == 0 && plain) ring_psi[rs + (e == 0 ? 0 : w + 1)] = colour_field(p, rr, rb);
+                        }
+                    }
+                    const bool full_l = !open_l && (HERMITE_SRC || wall_row || !plain_l);
+                    const bool full_r = !open_r && (HERMITE_SRC || wall_row || !plain_r);
+                    if ((tid == 0 && full_l) || (tid == 1 && full_r)) edge_full(L, Y, tid == 0 ? 0 : w + 1);
                 }
             }
         };
@@ -514,6 +561,10 @@ __global__ void __launch_bounds__(W, (FusedCfg<T, CV, W, NSLOT>::MINB)) k_step_f
             return;
         }
     }
+    // this block's stores are issued: the next step may launch (it still waits
+    // for this grid's completion before it reads anything); a block that
+    // triggered at its start does not trigger again
+    if (!(flags & FUSED_EARLY_NEXT)) asm volatile("griddepcontrol.launch_dependents;");
 }
 
 // --------------------------------------------------------- two-pass kernels
