@@ -55,8 +55,9 @@ class Result:
     admitted: float
     finished: float
     nodes: int
-    steps: int
+    steps: int                 # steps run (fewer than requested if the run failed)
     diag: dict = field(default_factory=dict)
+    failed: bool = False       # the state went non-finite; the request was retired early
 
     @property
     def latency(self) -> float:
@@ -153,7 +154,12 @@ def _stats(results: list[Result], makespan: float) -> dict:
     work = sum(r.nodes * r.steps for r in results)
     return {"requests": len(results), "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
-            "makespan_s": makespan, "mlups": work / makespan / 1e6, "updates": work}
+            "makespan_s": makespan, "mlups": work / makespan / 1e6, "updates": work,
+            "failed": sum(1 for r in results if r.failed)}
+
+
+def _failed(diag: dict) -> bool:
+    return diag.get("nonfinite", 0) != 0
 
 
 class Server:
@@ -239,9 +245,11 @@ class Server:
             retired = []
             for k in key:
                 s, r, adm, nb = active[k]
-                if s.t >= r.spec.steps:
-                    d = s.diagnostics(allow_unstable=True)
-                    results.append(Result(r.rid, r.arrival, adm, done, r.spec.nx * r.spec.ny, r.spec.steps, d))
+                # every member's FP64 diagnostics: a finished request returns them,
+                # and one whose state went non-finite is retired at once as failed
+                d = s.diagnostics(allow_unstable=True)
+                if s.t >= r.spec.steps or _failed(d):
+                    results.append(Result(r.rid, r.arrival, adm, done, r.spec.nx * r.spec.ny, s.t, d, _failed(d)))
                     retired.append(k)
             if retired:
                 batch.close()                   # no batch may refer to a freed simulation
@@ -259,9 +267,10 @@ class Server:
 
 
 def run_sequential(trace: list[tuple[float, SimSpec]], storage: int | None = 0,
-                   clock=time.perf_counter, sleep=time.sleep) -> tuple[list[Result], dict]:
+                   clock=time.perf_counter, sleep=time.sleep, check_every: int = 4000) -> tuple[list[Result], dict]:
     """Baseline: each request alone, in arrival order, through the single-simulation
-    path (FP32 storage by default)."""
+    path (FP32 storage by default), its state checked for non-finite values every
+    `check_every` steps (the server's longest chunk)."""
     reqs = sorted((Request(i, a, sp) for i, (a, sp) in enumerate(trace)), key=lambda r: r.arrival)
     results = []
     t0 = clock()
@@ -271,9 +280,13 @@ def run_sequential(trace: list[tuple[float, SimSpec]], storage: int | None = 0,
             sleep(r.arrival - now)
         adm = clock() - t0
         with start_simulation(r.spec, storage=storage) as s:
-            s.step(r.spec.steps)
-            d = s.diagnostics(allow_unstable=True)
-        results.append(Result(r.rid, r.arrival, adm, clock() - t0, r.spec.nx * r.spec.ny, r.spec.steps, d))
+            # the same failure check as the server's, at the same granularity
+            while True:
+                s.step(min(check_every, r.spec.steps - s.t))
+                d = s.diagnostics(allow_unstable=True)
+                if s.t >= r.spec.steps or _failed(d):
+                    break
+        results.append(Result(r.rid, r.arrival, adm, clock() - t0, r.spec.nx * r.spec.ny, s.t, d, _failed(d)))
     makespan = clock() - t0
     results.sort(key=lambda r: r.rid)
     return results, _stats(results, makespan)
