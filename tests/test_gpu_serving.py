@@ -53,3 +53,31 @@ def test_budget_limits_residency():
     results, stats = S.Server(budget_bytes=need, chunk=64).run(trace)
     assert stats["requests"] == 2
     assert results[1].admitted >= results[0].finished - 1e-9 or results[0].admitted >= results[1].finished - 1e-9
+
+
+def test_a_request_that_goes_non_finite_is_retired_as_failed():
+    """A physically unstable request (tau = 0.51 with the inlet at 0.1: the flow
+    blows up within a few hundred steps, in the method itself, without any fault)
+    is retired at the first check after its state goes non-finite, with the steps
+    it ran; the requests beside it finish with the results they have alone."""
+    L.load(build_if_missing=True)
+    good = _trace()[:2]
+    (_, sp0), (_, sp1) = good
+    bad = SimSpec(**{**sp0.as_dict(), "nx": 256, "ny": 64, "tau_r": 0.51, "tau_b": 0.51, "u_in_r": 0.1,
+                     "u_in_b": 0.1, "steps": 3000})
+    trace = [(0.0, sp0), (0.0, bad), (0.0, sp1)]
+    results, stats = S.Server(budget_bytes=2e9, chunk=64, max_chunk=500).run(trace)
+    by = {r.rid: r for r in results}
+    assert stats["failed"] == 1 and by[1].failed
+    assert 0 < by[1].steps < bad.steps and by[1].diag["nonfinite"] > 0
+    for rid, spec in ((0, sp0), (2, sp1)):
+        r = by[rid]
+        assert not r.failed and r.steps == spec.steps
+        with S.start_simulation(spec) as s:
+            s.step(spec.steps)
+            d = s.diagnostics()
+        for k in ("mass_r", "mass_b", "mom_x", "mom_y", "max_u", "area_b", "ux_b"):
+            assert r.diag[k] == d[k], (rid, k, r.diag[k], d[k])
+    # the sequential baseline applies the same check
+    seq, st = S.run_sequential(trace, check_every=500)
+    assert st["failed"] == 1 and seq[1].failed and seq[1].steps < bad.steps
