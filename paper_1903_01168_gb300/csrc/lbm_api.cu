@@ -658,7 +658,7 @@ bool use_fused(const lbm_sim *s) { return s->p.kernel != LBM_KERNEL_TWOPASS; }
 
 lbm_status sync_t0(lbm_sim *s) {
     if (s->dev_t0 != s->t) {
-        k_set_t0<<<1, 32, 0, s->stream>>>(s->d_desc, s->t);
+        k_set_times<<<1, 32, 0, s->stream>>>(s->d_desc, s->t, s->h.t_end);
         CK(cudaGetLastError());
         s->dev_t0 = s->t;
     }
@@ -1258,12 +1258,13 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
     lbm_sim *s = b->sims[0];
     if (n < 0) { set_err(s->err, "n < 0"); return LBM_EINVAL; }
     if (n == 0) return LBM_OK;
-    // resynchronise descriptors of members stepped outside the batch (their
-    // logical time no longer matches the batch descriptor's t0, clamped at the stop)
+    // resynchronise the descriptors of members stepped outside the batch (their
+    // logical time no longer matches the batch descriptor's t0, clamped at the
+    // stop) or given a new stop time since the batch last ran
     for (size_t i = 0; i < b->sims.size(); i++) {
         lbm_sim *m = b->sims[i];
         if (std::min(b->t_mirror[i], m->h.t_end) != m->t || b->t_stop[i] != m->h.t_end) {
-            k_set_t0<<<1, 32, 0, b->stream>>>(b->d_descs + i, m->t);
+            k_set_times<<<1, 32, 0, b->stream>>>(b->d_descs + i, m->t, m->h.t_end);
             CK(cudaGetLastError());
             b->t_mirror[i] = m->t;
         }

@@ -13,7 +13,7 @@
 //                  the same step as two plain node-parallel kernels with a
 //                  global scratch field (psi, q u) in between: the reference
 //                  GPU path, bit-identical to the fused one.
-//   k_init, k_fields, k_diag_*, k_advance, k_set_t0   support kernels.
+//   k_init, k_fields, k_diag_*, k_advance, k_set_times   support kernels.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -905,8 +905,13 @@ __global__ void k_advance(SimDesc *descs, int n, long long k) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) descs[i].t0 += k;
 }
 
-__global__ void k_set_t0(SimDesc *desc, long long t) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) desc->t0 = t;
+// A descriptor's start time and stop time (a batch keeps its own copies of its
+// members' descriptors, so both follow the member's logical time and stop here).
+__global__ void k_set_times(SimDesc *desc, long long t0, long long t_end) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        desc->t0 = t0;
+        desc->t_end = t_end;
+    }
 }
 
 #endif

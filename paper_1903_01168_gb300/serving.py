@@ -284,9 +284,10 @@ def run_sequential(trace: list[tuple[float, SimSpec]], storage: int | None = 0,
             while True:
                 s.step(min(check_every, r.spec.steps - s.t))
                 d = s.diagnostics(allow_unstable=True)
-                if s.t >= r.spec.steps or _failed(d):
+                ran = s.t
+                if ran >= r.spec.steps or _failed(d):
                     break
-        results.append(Result(r.rid, r.arrival, adm, clock() - t0, r.spec.nx * r.spec.ny, s.t, d, _failed(d)))
+        results.append(Result(r.rid, r.arrival, adm, clock() - t0, r.spec.nx * r.spec.ny, ran, d, _failed(d)))
     makespan = clock() - t0
     results.sort(key=lambda r: r.rid)
     return results, _stats(results, makespan)

@@ -243,6 +243,36 @@ def test_stop_times_in_a_batch():
         s.close()
 
 
+def test_stop_times_changed_after_the_batch_was_built():
+    """A stop time set on a member between two batch steps takes effect in the
+    batch (its device descriptor follows the member): the member ends at the new
+    stop, bit for bit where it ends alone, while the others run on; lifting the
+    stop lets it continue."""
+    names = ["random_ragged_mrt_hermite", "walls_bgk_gravity"]
+    sims = []
+    for nm in names:
+        nx, ny, kw, make, _ = CASES[nm]
+        s = L.Simulation(nx, ny, **_gpu_params(kw))
+        s.init_fields(*make())
+        sims.append(s)
+    b = L.Batch(sims)
+    b.step(16, use_graph=True)
+    sims[0].set_stop(16 + 5)
+    b.step(16, use_graph=True)
+    assert sims[0].t == 21 and sims[1].t == 32
+    nx, ny, kw, make, _ = CASES[names[0]]
+    assert sims[0].save_state() == _state_after(nx, ny, make(), 21, **_gpu_params(kw))
+    sims[0].set_stop(-1)
+    b.step(11, use_graph=False)
+    assert sims[0].t == 32 and sims[1].t == 43
+    assert sims[0].save_state() == _state_after(nx, ny, make(), 32, **_gpu_params(kw))
+    nx, ny, kw, make, _ = CASES[names[1]]
+    assert sims[1].save_state() == _state_after(nx, ny, make(), 43, **_gpu_params(kw))
+    b.close()
+    for s in sims:
+        s.close()
+
+
 def test_diagnostics_match_oracle_sums():
     nx, ny, kw, make, _ = CASES["walls_mrt_hermite"]
     f = make()
