@@ -46,8 +46,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic of one k_step_fused launch on this workload from an ncu capture of
 # `dram__bytes_read.sum + dram__bytes_write.sum`, valid only for the kernel
 # sources with this hash; reported as null otherwise.
-NCU_TRAFFIC = {"sources_sha": "37a3af57f6a2163e",
-               "bytes_per_launch": {0: 229037824 + 154469888, 1: 170611200 + 96857600}}
+NCU_TRAFFIC = {"sources_sha": "60141a825c48cb2c",
+               "bytes_per_launch": {0: 229121536 + 154410496, 1: 170580992 + 96698624, 2: 170623488 + 96513792}}
 
 
 def kernel_sources_sha() -> str:
