@@ -1271,7 +1271,8 @@ lbm_status lbm_batch_step(lbm_batch *b, long n, int use_graph) {
     }
     const int nsims = (int)b->sims.size();
     // Groups are independent simulations: each runs its k steps on its own stream,
-    // forked from and joined back into the batch stream.
+    // forked from and joined back into the batch stream (running them one after
+    // another on the batch stream, each with the whole GPU, was 5 % slower).
     auto run = [&](long k) -> lbm_status {
         if (b->groups.size() > 1) CK(cudaEventRecord(b->fork, b->stream));
         for (size_t gi = 0; gi < b->groups.size(); gi++) {
